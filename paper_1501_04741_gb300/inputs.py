@@ -1,0 +1,200 @@
+"""Seeded synthetic workloads shared by the CUDA path and the FP64 oracle.
+
+This module holds problem *descriptions* and seeded random inputs only: it
+contains none of the method's arithmetic (no equilibria, no collision, no
+streaming, no objective).  Both implementations read a :class:`Problem` and
+build their own node flags, tables and initial states from it.
+
+Workloads follow the paper's two channel test cases (Sec. 4, Tab. "tab:cases")
+and the synthetic stand-ins derived from them:
+
+* ``channel2d``  - D2Q9 BGK channel 128x64, body force, bounce-back walls on
+  y, periodic x, porosity on a central 32x32 design block; viscous dissipation.
+* ``mixer3d``    - D3Q19 MRT square-channel mixer 256x128x128 with two D3Q7
+  passive scalars (inlet halves c=0/1 and the complement), velocity inlet,
+  pressure outlet; outlet scalar variance averaged over the last 500 steps
+  (Sec. 4.1, Eq. "mixing:obj" is offered as ``mixflux``).
+* ``exchanger3d`` - D3Q19 BGK + D3Q7 temperature heat exchanger 512x256x256,
+  hot bottom patch T=1, inlet T=0, Pr=0.7; outlet heat flux minus 0.1 times
+  the pressure drop (Sec. 4.2, Eq. "exchanger:obj").
+
+Porosity naming: ``theta`` is the solid fraction (0 = fluid, 1 = solid), i.e.
+``theta = 1 - w`` with the paper's ``w`` of Sec. 3.2.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Problem:
+    """Plain description of one adjoint-LBM problem (no arithmetic)."""
+
+    lattice: str = "D2Q9"            # "D2Q9" | "D3Q19" (fluid lattice, Sec. 3)
+    dims: tuple = (128, 64, 1)       # (Lx, Ly, Lz); Lz == 1 for 2D
+    collision: str = "BGK"           # "BGK" (Eq. SRT) | "MRT" (Sec. 3.1)
+    tau: float = 0.8                 # 1/omega = tau = 0.5 + 3 nu (Sec. 3.1)
+    s_other: float = 1.2             # MRT rate of non-stress, non-conserved moments
+    force: tuple = (0.0, 0.0, 0.0)   # body acceleration g (EDM forcing, Sec. 3.1)
+    walls: str = "y"                 # axes carrying bounce-back wall planes at both ends
+    channel: str = "periodic"        # "periodic" in x | "inlet_outlet" (Zou-He x faces)
+    u_in: float = 0.05               # velocity inlet speed (x = 0 face)
+    rho_out: float = 1.0             # pressure outlet density (x = Lx-1 face)
+    nscalars: int = 0                # passive scalar lattices (D3Q7 in 3D, D2Q9 in 2D)
+    alpha_fluid: float = 0.0         # scalar diffusivity in fluid (theta = 0)
+    alpha_solid: float = 0.0         # scalar diffusivity in solid (theta = 1)
+    scalar_inlet: str = "zero"       # "zero" | "halves" (c = 0 for y < Ly/2, else 1)
+    hot: tuple = ()                  # (x0, x1, z0, z1): y = 0 wall nodes with T = T_hot
+    T_hot: float = 1.0
+    porosity: str = "linear"         # G(theta): "linear" 1-theta | "power" 1-theta^q | "ramp"
+    porosity_q: float = 1.0
+    objective: str = "dissipation"   # "none"|"dissipation"|"variance"|"heatflux_dp"|"mixflux"
+    obj_window: int = 0              # 0: J = F(f^N); K > 0: mean of F(f^n), N-K < n <= N
+    nsteps: int = 2000               # horizon N of the unsteady problem
+    design: tuple = (48, 80, 16, 48, 0, 1)   # (x0, x1, y0, y1, z0, z1) design box
+    precision: str = "fp32"          # population storage on the GPU: fp32 | bf16 | fp16
+    ckpt_every: int = 0              # level-1 checkpoint stride of the adjoint schedule
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.dims[0]) * int(self.dims[1]) * int(self.dims[2])
+
+    @property
+    def is3d(self) -> bool:
+        return self.lattice == "D3Q19"
+
+    def replace(self, **kw) -> "Problem":
+        return dataclasses.replace(self, **kw)
+
+
+# ---------------------------------------------------------------------------
+# Workload presets (parameters only)
+# ---------------------------------------------------------------------------
+
+def channel2d(**kw) -> Problem:
+    """D2Q9 BGK channel 128x64, tau=0.8, g=(1e-5,0), walls y, periodic x."""
+    p = Problem(lattice="D2Q9", dims=(128, 64, 1), collision="BGK", tau=0.8,
+                force=(1e-5, 0.0, 0.0), walls="y", channel="periodic",
+                objective="dissipation", obj_window=0, nsteps=2000,
+                design=(48, 80, 16, 48, 0, 1))
+    return p.replace(**kw)
+
+
+def mixer3d(**kw) -> Problem:
+    """D3Q19 MRT mixer 256x128x128 + two D3Q7 scalars, tau=0.6.
+
+    Diffusivity keeps the paper's mixer ratio nu/alpha = 0.02/0.003 (Tab.
+    "tab:cases") for both phases (alpha_solid = alpha_fluid, as in the paper).
+    """
+    tau = 0.6
+    nu = (tau - 0.5) / 3.0
+    alpha = nu * 0.003 / 0.02
+    Lx, Ly, Lz = 256, 128, 128
+    p = Problem(lattice="D3Q19", dims=(Lx, Ly, Lz), collision="MRT", tau=tau,
+                walls="yz", channel="inlet_outlet", u_in=0.05, rho_out=1.0,
+                nscalars=2, alpha_fluid=alpha, alpha_solid=alpha,
+                scalar_inlet="halves", objective="variance", obj_window=500,
+                nsteps=10000, design=(64, 192, 16, 112, 16, 112), ckpt_every=500)
+    return p.replace(**kw)
+
+
+def exchanger3d(**kw) -> Problem:
+    """D3Q19 BGK + D3Q7 temperature heat exchanger 512x256x256, tau=0.55.
+
+    Pr = nu/alpha_fluid = 0.7, alpha_solid = 1 (Tab. "tab:cases"); the D x D
+    hot plate sits on the bottom wall in the middle of the channel and the
+    design region is the middle 3/7 of the length (Sec. 4.2).
+    """
+    tau = 0.55
+    nu = (tau - 0.5) / 3.0
+    Lx, Ly, Lz = 512, 256, 256
+    x0 = Lx // 2 - Ly // 2
+    p = Problem(lattice="D3Q19", dims=(Lx, Ly, Lz), collision="BGK", tau=tau,
+                walls="yz", channel="inlet_outlet", u_in=0.05, rho_out=1.0,
+                nscalars=1, alpha_fluid=nu / 0.7, alpha_solid=1.0,
+                scalar_inlet="zero", hot=(x0, x0 + Ly, 0, Lz), T_hot=1.0,
+                objective="heatflux_dp", obj_window=0, nsteps=1000,
+                design=(2 * Lx // 7, 5 * Lx // 7, 1, Ly - 1, 1, Lz - 1))
+    return p.replace(**kw)
+
+
+def scaled(p: Problem, dims, nsteps=None, **kw) -> Problem:
+    """The same physics on another lattice size (design box and hot patch scaled)."""
+    Lx0, Ly0, Lz0 = p.dims
+    Lx, Ly, Lz = dims
+    d = p.design
+
+    def sx(a):
+        return int(round(a * Lx / Lx0))
+
+    def sy(a):
+        return int(round(a * Ly / Ly0))
+
+    def sz(a):
+        return int(round(a * Lz / Lz0)) if Lz0 > 1 else a
+
+    design = (sx(d[0]), max(sx(d[1]), sx(d[0]) + 1), sy(d[2]), max(sy(d[3]), sy(d[2]) + 1),
+              sz(d[4]), max(sz(d[5]), sz(d[4]) + 1))
+    hot = p.hot
+    if hot:
+        hot = (sx(hot[0]), sx(hot[1]), sz(hot[2]), sz(hot[3]))
+    out = p.replace(dims=tuple(int(v) for v in dims), design=design, hot=hot)
+    if nsteps is not None:
+        out = out.replace(nsteps=int(nsteps))
+    return out.replace(**kw)
+
+
+# ---------------------------------------------------------------------------
+# Seeded porosity fields (FP32, the same bytes go to both implementations)
+# ---------------------------------------------------------------------------
+
+def design_mask(p: Problem) -> np.ndarray:
+    """Boolean (Lz, Ly, Lx) mask of the design box."""
+    Lx, Ly, Lz = p.dims
+    x0, x1, y0, y1, z0, z1 = p.design
+    m = np.zeros((Lz, Ly, Lx), dtype=bool)
+    m[max(z0, 0):min(z1, Lz), max(y0, 0):min(y1, Ly), max(x0, 0):min(x1, Lx)] = True
+    return m
+
+
+def theta_uniform(p: Problem, seed: int) -> np.ndarray:
+    """theta ~ U[0,1] on the design box, 0 elsewhere; float32 (Lz, Ly, Lx)."""
+    rng = np.random.default_rng(seed)
+    Lx, Ly, Lz = p.dims
+    th = np.zeros((Lz, Ly, Lx), dtype=np.float32)
+    m = design_mask(p)
+    th[m] = rng.random(int(m.sum()), dtype=np.float64).astype(np.float32)
+    return th
+
+
+def theta_grf(p: Problem, seed: int, sigma: float = 4.0) -> np.ndarray:
+    """Smoothed Gaussian random field in [0,1] on the design box.
+
+    White noise filtered by a Gaussian of width ``sigma`` lattice units (FFT,
+    periodic), min-max rescaled to [0,1] over the design box in FP64, then cast
+    to float32 once.  Zero outside the design box.
+    """
+    rng = np.random.default_rng(seed)
+    Lx, Ly, Lz = p.dims
+    noise = rng.standard_normal((Lz, Ly, Lx))
+    kz = np.fft.fftfreq(Lz)[:, None, None]
+    ky = np.fft.fftfreq(Ly)[None, :, None]
+    kx = np.fft.fftfreq(Lx)[None, None, :]
+    k2 = (2 * math.pi) ** 2 * (kx ** 2 + ky ** 2 + kz ** 2)
+    field_ = np.real(np.fft.ifftn(np.fft.fftn(noise) * np.exp(-0.5 * sigma ** 2 * k2)))
+    m = design_mask(p)
+    th = np.zeros((Lz, Ly, Lx), dtype=np.float32)
+    if m.any():
+        v = field_[m]
+        lo, hi = float(v.min()), float(v.max())
+        th[m] = ((v - lo) / max(hi - lo, 1e-300)).astype(np.float32)
+    return th
+
+
+def random_state(shape, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Seeded float64 normal array (for duality tests and random adjoints)."""
+    return np.random.default_rng(seed).standard_normal(shape) * scale

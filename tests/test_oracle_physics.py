@@ -1,0 +1,250 @@
+"""Pins of the oracle's primal iteration: Lemma 1, conservation laws, the
+Poiseuille closed form, dissipation, Zou-He, porosity limits and scalar
+diffusion (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle.model import FLUID, INLET, OUTLET, WALL, HOT, build_flags
+from oracle.solver import Oracle
+from paper_1501_04741_gb300 import inputs
+
+
+def _rand_state(o, seed, scale=0.02):
+    rng = np.random.default_rng(seed)
+    m = o.model
+    F = o.initial().clone()
+    F[:m.Q] *= torch.tensor(1 + scale * rng.standard_normal(F[:m.Q].shape))
+    if m.NS:
+        F[m.Q:] = torch.tensor(0.1 * rng.random(F[m.Q:].shape))
+    return F
+
+
+@pytest.mark.parametrize("lattice,dims,ns", [("D2Q9", (7, 5, 1), 1), ("D3Q19", (5, 4, 3), 2)])
+def test_lemma1_streaming_is_a_permutation(lattice, dims, ns):
+    # Lemma 1 (Sec. 2.2): S is unitary; S^-1 S = identity bit-exactly, sums
+    # are invariant and <a, S b> = <S^-1 a, b>.
+    P = inputs.Problem(lattice=lattice, dims=dims, walls="", nscalars=ns, objective="none")
+    o = Oracle(P, np.zeros(dims[::-1], np.float32))
+    rng = np.random.default_rng(0)
+    a = torch.tensor(rng.standard_normal((o.model.M,) + o.shape))
+    b = torch.tensor(rng.standard_normal((o.model.M,) + o.shape))
+    assert torch.equal(o.unstream(o.stream(a)), a)
+    assert torch.equal(o.stream(o.unstream(a)), a)
+    assert abs(float(o.stream(a).sum() - a.sum())) < 1e-12
+    lhs = float((a * o.stream(b)).sum())
+    rhs = float((o.unstream(a) * b).sum())
+    assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+    # the shift moves f_j from x to x + e_j (periodic)
+    e = o.model.E_all[3]
+    z, y, x = dims[2] - 1, 2, 3
+    val = o.stream(a)[3, (z + e[2]) % dims[2], (y + e[1]) % dims[1], (x + e[0]) % dims[0]]
+    assert float(val) == float(a[3, z, y, x])
+
+
+@pytest.mark.parametrize("coll", ["BGK", "MRT"])
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_periodic_mass_and_momentum_conservation(coll, lattice):
+    dims = (6, 5, 1) if lattice == "D2Q9" else (4, 4, 3)
+    P = inputs.Problem(lattice=lattice, collision=coll, dims=dims, walls="", tau=0.7,
+                       objective="none")
+    o = Oracle(P, np.zeros(dims[::-1], np.float32))
+    F = _rand_state(o, 1)
+    m = o.model
+    mass0 = float(F[:m.Q].sum())
+    mom0 = torch.einsum("qa,q...->a", m.E, F[:m.Q])
+    with torch.no_grad():
+        for _ in range(100):
+            F = o.step(F)
+    assert abs(float(F[:m.Q].sum()) - mass0) < 1e-12 * mass0
+    mom = torch.einsum("qa,q...->a", m.E, F[:m.Q])
+    assert (mom - mom0).abs().max() < 1e-12 * mass0
+
+
+def test_body_force_momentum_growth_is_exact():
+    # Exact-Difference forcing (Sec. 3.1): u_post = u_pre + g, so the total
+    # momentum grows by exactly (total mass) * g per step.
+    dims = (5, 4, 1)
+    g = (3e-5, -2e-5, 0.0)
+    P = inputs.Problem(lattice="D2Q9", dims=dims, walls="", force=g, objective="none")
+    o = Oracle(P, np.zeros(dims[::-1], np.float32))
+    F = _rand_state(o, 2)
+    m = o.model
+    mass = float(F[:m.Q].sum())
+    mom0 = torch.einsum("qa,q...->a", m.E, F[:m.Q])
+    nsteps = 50
+    with torch.no_grad():
+        for _ in range(nsteps):
+            F = o.step(F)
+    mom = torch.einsum("qa,q...->a", m.E, F[:m.Q])
+    expect = mom0 + nsteps * mass * torch.tensor(g, dtype=torch.float64)
+    assert (mom - expect).abs().max() < 1e-13
+
+
+def test_walls_conserve_mass():
+    P = inputs.channel2d(dims=(9, 7, 1), design=(2, 6, 2, 5, 0, 1), objective="none")
+    th = inputs.theta_uniform(P, 3)
+    o = Oracle(P, th)
+    F = _rand_state(o, 3)
+    mass0 = float(F[:9].sum())
+    with torch.no_grad():
+        for _ in range(200):
+            F = o.step(F)
+    assert abs(float(F[:9].sum()) - mass0) < 1e-13 * mass0
+
+
+def _poiseuille(coll, tau, Ly=10, g=1e-6, viscous_times=14):
+    P = inputs.channel2d(dims=(3, Ly, 1), collision=coll, tau=tau, force=(g, 0, 0),
+                         design=(0, 0, 0, 0, 0, 1), objective="dissipation")
+    o = Oracle(P, np.zeros((1, Ly, 3), np.float32))
+    nu = (tau - 0.5) / 3
+    F = o.initial()
+    with torch.no_grad():
+        for _ in range(int(viscous_times * (Ly - 2) ** 2 / nu)):
+            F = o.step(F)
+    m = o.model
+    f = F[:9].reshape(9, -1)
+    rho = f.sum(0)
+    # physical velocity of the Exact-Difference scheme: mean of pre and post
+    ux = ((m.E.T @ f)[0] / rho + g / 2).reshape(Ly, 3)[:, 0].numpy()
+    return o, F, ux, nu
+
+
+def test_poiseuille_exact_at_magic_tau():
+    # BGK with bounce-back walls reproduces the parabolic Poiseuille profile
+    # exactly, with the wall half-way between wall and fluid nodes, when
+    # (tau - 1/2)^2 = 3/16 (He, Zou, Luo & Dembo 1997): a closed-form pin of
+    # the collision, the forcing, bounce-back and periodic streaming.
+    g, Ly = 1e-6, 10
+    tau = 0.5 + math.sqrt(3.0 / 16.0)
+    o, F, ux, nu = _poiseuille("BGK", tau, Ly=Ly, g=g)
+    y = np.arange(Ly)
+    a, b = 0.5, Ly - 1.5
+    exact = g / (2 * nu) * (y - a) * (b - y)
+    rel = np.abs(ux[1:-1] - exact[1:-1]).max() / exact.max()
+    assert rel < 1e-9
+
+
+@pytest.mark.parametrize("tau", [0.8, 0.6])
+def test_poiseuille_profile_with_bgk_slip(tau):
+    # Away from the magic tau, BGK + bounce-back adds a uniform slip
+    # u_s = g (16 (tau-1/2)^2 - 3) / (24 nu) to the parabola (same reference).
+    g, Ly = 1e-6, 10
+    o, F, ux, nu = _poiseuille("BGK", tau, Ly=Ly, g=g)
+    y = np.arange(Ly)
+    a, b = 0.5, Ly - 1.5
+    exact = g / (2 * nu) * (y - a) * (b - y) + g * (16 * (tau - 0.5) ** 2 - 3) / (24 * nu)
+    rel = np.abs(ux[1:-1] - exact[1:-1]).max() / exact.max()
+    assert rel < 2e-3
+    # u_max within 1e-3 of the closed form once the stated slip is included
+    assert abs(ux.max() - exact.max()) / exact.max() < 1e-3 + 1e-2 * abs(exact.max() - exact[1])
+
+
+def test_dissipation_objective_closed_form():
+    # Steady Poiseuille: 2 rho nu S:S = rho nu (du/dy)^2 with
+    # du/dy = g (a + b - 2y) / (2 nu), summed over fluid nodes (3 columns).
+    g, Ly, tau = 1e-6, 10, 0.8
+    o, F, ux, nu = _poiseuille("BGK", tau, Ly=Ly, g=g)
+    a, b = 0.5, Ly - 1.5
+    phi = sum(nu * (g / (2 * nu) * (a + b - 2 * y)) ** 2 for y in range(1, Ly - 1)) * 3
+    J = float(o.F_obj(F))
+    assert abs(J - phi) / phi < 1e-6
+
+
+def _mixer_small(**kw):
+    return inputs.scaled(inputs.mixer3d(), (10, 6, 6), nsteps=20, obj_window=4, **kw)
+
+
+def test_flags_channel_geometry():
+    P = inputs.scaled(inputs.exchanger3d(), (14, 8, 8))
+    fl = build_flags(P)
+    assert fl.dtype == np.uint8
+    assert (fl[1:-1, 1:-1, 0] == INLET).all() and (fl[1:-1, 1:-1, -1] == OUTLET).all()
+    x0, x1, z0, z1 = P.hot
+    assert (fl[z0:z1, 0, x0:x1] == HOT).all()
+    hot = np.zeros_like(fl, dtype=bool)
+    hot[z0:z1, 0, x0:x1] = True
+    assert (fl[0][~hot[0]] == WALL).all() and (fl[-1][~hot[-1]] == WALL).all()
+    assert (fl[1:-1, -1, :] == WALL).all()
+    assert (fl[:, 0, :][~hot[:, 0, :]] == WALL).all()
+    assert (fl[1:-1, 1:-1, 1:-1] == FLUID).all()
+
+
+def test_zou_he_prescribed_values_after_collision():
+    # Zou & He (Sec. 3): after the node operator the inlet node carries
+    # u = u_in and the outlet node rho = rho_out.
+    P = _mixer_small(collision="BGK")
+    o = Oracle(P, np.zeros(P.dims[::-1], np.float32))
+    F = _rand_state(o, 5, scale=0.01)
+    post = o.collide(F).reshape(o.model.M, -1)
+    m = o.model
+    f = post[:m.Q]
+    rho = f.sum(0)
+    u = (m.E.T @ f) / rho
+    inl = o.flags == INLET
+    out = o.flags == OUTLET
+    assert (u[0, inl] - P.u_in).abs().max() < 1e-14
+    assert u[1:, inl].abs().max() < 1e-14
+    assert (rho[out] - P.rho_out).abs().max() < 1e-14
+    assert u[1:, out].abs().max() < 1e-14
+    # inlet scalars sit at equilibrium with the prescribed halves profile
+    T0 = post[m.Q:m.Q + m.Qs].sum(0)
+    T1 = post[m.Q + m.Qs:].sum(0)
+    c = (o.y >= P.dims[1] // 2).double()
+    assert (T0[inl] - c[inl]).abs().max() < 1e-14
+    assert (T1[inl] - (1 - c[inl])).abs().max() < 1e-14
+
+
+def test_porosity_limits():
+    # Sec. 3.2: G(fluid) = 1 leaves the run unchanged (bit-exact with theta = 0)
+    # and G(solid) = 0 gives u_post = 0 (no body force).
+    P = inputs.channel2d(dims=(12, 8, 1), design=(3, 9, 2, 6, 0, 1), force=(0, 0, 0),
+                         objective="none")
+    o0 = Oracle(P, np.zeros((1, 8, 12), np.float32))
+    F = _rand_state(o0, 7)
+    o_same = Oracle(P.replace(design=(0, 0, 0, 0, 0, 1)), np.zeros((1, 8, 12), np.float32))
+    assert torch.equal(o0.step(F), o_same.step(F))
+    th = np.zeros((1, 8, 12), np.float32)
+    th[0, 2:6, 3:9] = 1.0
+    o1 = Oracle(P, th)
+    post = o1.collide(F).reshape(o1.model.M, -1)
+    j = o1.model.E.T @ post[:9]
+    solid = torch.tensor(th.reshape(-1) == 1.0)
+    assert j[:, solid].abs().max() < 1e-16
+
+
+def test_scalar_diffusion_decay_and_conservation():
+    # Pure diffusion (u = 0, periodic): sum T is conserved and a Fourier mode
+    # decays at rate alpha k^2 up to O(k^2) lattice corrections.
+    L = 32
+    alpha = 0.05
+    P = inputs.Problem(lattice="D3Q19", dims=(L, 2, 2), walls="", nscalars=1,
+                       alpha_fluid=alpha, alpha_solid=alpha, objective="none")
+    o = Oracle(P, np.zeros((2, 2, L), np.float32))
+    F = o.initial().clone()
+    k = 2 * math.pi / L
+    x = torch.arange(L, dtype=torch.float64)
+    T0 = 0.5 + 0.1 * torch.sin(k * x)
+    m = o.model
+    F[m.Q:] = (m.ws[:, None] * T0[None, :]).view(m.Qs, 1, 1, L)
+    total0 = float(F[m.Q:].sum())
+    nsteps = 200
+    with torch.no_grad():
+        for _ in range(nsteps):
+            F = o.step(F)
+    T = F[m.Q:].sum(0)[0, 0]
+    amp = float(((T - 0.5) * torch.sin(k * x)).sum() * 2 / L)
+    rate = -math.log(amp / 0.1) / nsteps
+    assert abs(rate - alpha * k * k) / (alpha * k * k) < 0.02
+    assert abs(float(F[m.Q:].sum()) - total0) < 1e-12 * total0
+
+
+def test_uniform_scalar_has_zero_variance():
+    P = _mixer_small(scalar_inlet="zero", nscalars=1)
+    o = Oracle(P, np.zeros(P.dims[::-1], np.float32))
+    F = o.initial().clone()
+    m = o.model
+    F[m.Q:] = 0.3 * m.ws.view(-1, 1, 1, 1)
+    assert abs(float(o.F_obj(F))) < 1e-15
