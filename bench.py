@@ -1,0 +1,323 @@
+"""Benchmark of the adjoint-LBM sensitivity solve (primal + adjoint MLUPS).
+
+One bench step is one full unsteady sensitivity solve of the D3Q19 MRT
+mixer (256x128x128 nodes, two D3Q7 passive scalars, velocity inlet and
+pressure outlet, tau = 0.6, theta ~ U[0,1] on the 128x96x96 design region,
+J = outlet scalar variance averaged over the last 500 steps): 10000 primal
+steps, then 10000 adjoint steps with level-1 checkpoints every 500 steps
+and recomputation of the states in between, accumulating dJ/dtheta in FP64.
+
+value = nodes * (primal steps + adjoint steps) / seconds / 1e6 (recomputed
+primal steps are work, not credit).  Inputs (550 MB of populations per
+state) are larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With torchrun (N > 1) every rank solves its own independent replica (the
+path does not shard in this build: replicas only) and rank 0 prints the
+aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1501_04741_gb300 import inputs  # noqa: E402
+
+METRIC = "primal+adjoint MLUPS & % HBM roofline"
+UNIT = "MLUPS"
+
+# algorithmic bytes per node update (FP32 populations, 33 densities):
+#   primal : read 33 x 4 + write 33 x 4 + theta 4 + flag 1
+#   adjoint: read lambda 33 x 4 + read f 33 x 4 + write lambda 33 x 4
+#            + theta 4 + flag 1 + FP64 gradient read + write 16
+def bytes_per_node(M: int, storage: int, kind: str) -> int:
+    if kind == "primal":
+        return M * storage * 2 + 5
+    return M * 4 * 2 + M * storage + 21
+
+
+def workload(args) -> inputs.Problem:
+    P = inputs.mixer3d()
+    if args.nsteps:
+        P = P.replace(nsteps=args.nsteps, obj_window=min(P.obj_window, args.nsteps))
+    if args.precision != "fp32":
+        P = P.replace(precision=args.precision)
+    return P
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = self.rows
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle, timed on the host cores (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+ORACLE_SAMPLE_DIMS = (96, 48, 48)
+ORACLE_SAMPLE_STEPS = 6
+
+
+def oracle_sample(P: inputs.Problem):
+    """Time the FP64 oracle on a bounded sample of the workload: the same
+    physics on a 96x48x48 sub-lattice, 6 primal then 6 adjoint steps."""
+    import torch
+    from oracle.solver import Oracle
+    Ps = inputs.scaled(P, ORACLE_SAMPLE_DIMS, nsteps=ORACLE_SAMPLE_STEPS,
+                       obj_window=min(P.obj_window, ORACLE_SAMPLE_STEPS))
+    o = Oracle(Ps, inputs.theta_uniform(Ps, 0))
+    t0 = time.perf_counter()
+    _, traj = o.primal()
+    o.adjoint(traj)
+    dt = time.perf_counter() - t0
+    updates = o.n * ORACLE_SAMPLE_STEPS * 2
+    sample = (f"{Ps.lattice} {Ps.collision} + {Ps.nscalars} scalars on "
+              f"{'x'.join(map(str, ORACLE_SAMPLE_DIMS))}, {ORACLE_SAMPLE_STEPS} primal + "
+              f"{ORACLE_SAMPLE_STEPS} adjoint steps (FP64 oracle)")
+    return updates / dt / 1e6, dt, torch.get_num_threads(), sample
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    P = workload(args)
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(P)
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        v, dt, cores, sample = oracle_sample(P)
+        vals.append(v)
+    wall = time.perf_counter() - t_all
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * wall / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(P, args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(P, args):
+    return {"workload": "mixer3d", "lattice": P.lattice, "collision": P.collision,
+            "dims": list(P.dims), "nscalars": P.nscalars, "tau": P.tau,
+            "primal_steps": P.nsteps, "adjoint_steps": P.nsteps, "ckpt_every": P.ckpt_every,
+            "objective": P.objective, "obj_window": P.obj_window, "precision": P.precision,
+            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{args.gpus}"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1501_04741_gb300.albm import Solver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    P = workload(args)
+    theta = inputs.theta_uniform(P, rank)
+    stream = torch.cuda.Stream()
+    th_dev = torch.from_numpy(theta.reshape(-1)).cuda()
+    s = Solver(P, th_dev, stream=stream, mem_budget=args.mem_budget)
+    N = s.N
+    M = s.M
+    storage = {"fp32": 4, "bf16": 2, "fp16": 2}[P.precision]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    # warm-up (allocates the state pool too)
+    for _ in range(args.warmup):
+        s.run()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    s.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            s.run()
+        ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = s.profile_read()
+    s.profile(False)
+    clk = clocks.stop()
+    J = s.objective()
+    recompute = s.recompute_steps()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    updates_per_step = N * P.nsteps * 2
+    value = world * updates_per_step * args.steps / (ms_max / 1e3) / 1e6
+
+    # kernel-level numbers from the live event record
+    n_p, ms_p = prof["primal"]
+    n_r, ms_r = prof["recompute"]
+    n_a, ms_a = prof["adjoint"]
+    peak, peak_kind = _peaks()
+    bp = bytes_per_node(M, storage, "primal")
+    ba = bytes_per_node(M, storage, "adjoint")
+    prim_ms = (ms_p + ms_r) / max(n_p + n_r, 1)
+    adj_ms = ms_a / max(n_a, 1)
+    prim_gbs = bp * N / (prim_ms / 1e3) / 1e9
+    adj_gbs = ba * N / (adj_ms / 1e3) / 1e9
+    share_adj = ms_a / max(ms_p + ms_r + ms_a, 1e-9)
+    dom = "adjoint" if share_adj >= 0.5 else "primal"
+    ach = adj_gbs if dom == "adjoint" else prim_gbs
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if rank == 0 or True:
+        th_host = torch.from_numpy(theta.reshape(-1)).pin_memory()
+        g_host = torch.empty(N, dtype=torch.float64).pin_memory()
+        s2 = s
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.e2e_steps)):
+            s2.set_theta(th_host.numpy())
+            s2.run()
+            s2.gradient(g_host.numpy())
+            s2.objective()
+        barrier()
+        dt = time.perf_counter() - t0
+        e2e = {"value": world * updates_per_step * max(1, args.e2e_steps) / dt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(N * 4), "d2h_bytes_per_step": int(N * 8 + 16 * (P.nsteps + 1))}
+    launches = args.steps * (P.nsteps + 1 + P.nsteps + 1) + recompute
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, cores, sample = oracle_sample(P)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if P.precision == "fp32" else f"f32 ({P.precision} storage)",
+            "data": "synthetic", "config": _config(P, args),
+            "roofline": {"bound": "hbm", "kernel": f"{dom}_kernel", "achieved": ach,
+                         "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "peak_source": peak_kind, "traffic": None},
+            "kernels": {
+                "primal": {"launches": n_p + n_r, "avg_ms": prim_ms, "GB_s": prim_gbs,
+                           "bytes_per_node": bp, "MLUPS": N / (prim_ms / 1e3) / 1e6},
+                "adjoint": {"launches": n_a, "avg_ms": adj_ms, "GB_s": adj_gbs,
+                            "bytes_per_node": ba, "MLUPS": N / (adj_ms / 1e3) / 1e6},
+                "share_adjoint": share_adj, "recompute_steps_per_solve": recompute},
+            "J": J,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nsteps", type=int, default=0, help="override the 10000-step horizon")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--mem-budget", type=float, default=0.0)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,218 @@
+/*
+ * albm.h - C ABI of the GB300 adjoint Lattice Boltzmann library (libalbm.so).
+ *
+ * The operations follow the paper's statement of the problem
+ * (Laniewski-Wollk & Rokicki, "Adjoint Lattice Boltzmann for Topology
+ * Optimization on multi-GPU architecture"):
+ *
+ *   lattice L = {0..Lx-1} x {0..Ly-1} x {0..Lz-1}, densities f: L -> R^M,
+ *   one step  f^{n+1}_j(x + e_j) = W^x_j(f^n(x), theta)      (Sec. 2.1,
+ *             Eq. "normal:iteration", shifts periodic),
+ *   objective J = sum_n c_n sum_x F^x(f^n(x))                (Eq.
+ *             "objective:function", with time weights c_n),
+ *   adjoint   lambda^n_k(x) = sum_j lambda^{n+1}_j(x + e_j) dW^x_j/df_k
+ *                             + c_n dF^x/df_k                (Eqs.
+ *             "adjoint:iteration" and "adjoint:operator", unsteady form),
+ *   gradient  dJ/dtheta(x) = sum_n sum_j lambda^{n+1}_j(x + e_j) dW^x_j/dtheta
+ *                            + sum_n c_n dF^x/dtheta         (Eq.
+ *             "adjoint:derivative", accumulated over the time steps).
+ *
+ * Conventions shared by every call:
+ *  - Node index idx = x + Lx*(y + Ly*z) (x fastest).  Per-node arrays hold N =
+ *    Lx*Ly*Lz entries.  Population arrays are structure-of-arrays: density m
+ *    of node idx at [m*N + idx], m = 0..M-1 with the Q fluid populations
+ *    first (paper order e1..e19, or its z = 0 members in 2D) followed by
+ *    each scalar lattice's Qs populations.
+ *  - theta is the solid fraction per node (0 = fluid, 1 = solid), i.e.
+ *    1 - w for the paper's w of Sec. 3.2.
+ *  - Pointer arguments marked "host or device" may point to host memory
+ *    (pageable or pinned) or to device memory of the handle's device; the
+ *    library copies through unified addressing.  The caller keeps ownership
+ *    of every pointer it passes; the library keeps none of them.
+ *  - Every call returns an lbm_status and never throws; lbm_last_error()
+ *    gives a message for the last failure on a handle.
+ *  - Calls are asynchronous on the handle's CUDA stream unless stated.
+ *  - A handle is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef ALBM_H
+#define ALBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx* lbm_handle;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,        /* invalid argument or unsupported combination   */
+  LBM_ERR_OOM = 2,        /* device allocation failed                      */
+  LBM_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed   */
+  LBM_ERR_NONFINITE = 4,  /* a non-finite value was found in the state     */
+  LBM_ERR_TIMEOUT = 5,    /* a bounded device wait expired                 */
+  LBM_ERR_STATE = 6       /* call out of order (e.g. adjoint before primal)*/
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
+typedef enum { LBM_BGK = 0, LBM_MRT = 1 } lbm_collision;
+typedef enum { LBM_FP32 = 0, LBM_BF16 = 1, LBM_FP16 = 2 } lbm_precision;
+typedef enum { LBM_POR_LINEAR = 0, LBM_POR_POWER = 1, LBM_POR_RAMP = 2 } lbm_porosity;
+typedef enum {
+  LBM_OBJ_NONE = 0,
+  LBM_OBJ_DISSIPATION = 1, /* sum over FLUID nodes of 2 rho nu S:S            */
+  LBM_OBJ_VARIANCE = 2,    /* outlet variance of scalar 0                     */
+  LBM_OBJ_HEATFLUX_DP = 3, /* outlet sum u_x T (Eq. exchanger:obj) - 0.1 dp   */
+  LBM_OBJ_MIXFLUX = 4      /* outlet sum u_x (1 - T^2) (Eq. mixing:obj)        */
+} lbm_objective_kind;
+
+/* Node types of the uint8 flag array (Sec. 3: interior, inlet/outlet, wall). */
+enum {
+  LBM_NODE_FLUID = 0,  /* FMRT/BGK with Exact-Difference forcing and porosity */
+  LBM_NODE_WALL = 1,   /* full-way bounce-back of every lattice               */
+  LBM_NODE_INLET = 2,  /* Zou-He velocity inlet on the x = 0 face             */
+  LBM_NODE_OUTLET = 3, /* Zou-He pressure outlet on the x = Lx-1 face         */
+  LBM_NODE_HOT = 4     /* fluid bounce-back, scalars at equilibrium T_hot     */
+};
+
+/* Problem description (plain values; copied by lbm_create). */
+typedef struct {
+  int lattice;          /* lbm_lattice                                       */
+  int nx, ny, nz;       /* lattice size; nz = 1 for D2Q9                      */
+  int collision;        /* lbm_collision (Sec. 3.1: Eq. SRT or FMRT)          */
+  double tau;           /* 1/omega = tau = 0.5 + 3 nu (0.5 < tau)             */
+  double s_other;       /* MRT rate of the non-stress, non-conserved moments  */
+  double force[3];      /* body acceleration g (Exact-Difference forcing)     */
+  int walls;            /* bit 0: wall planes y = 0, Ly-1; bit 1: z = 0, Lz-1 */
+  int inlet_outlet;     /* 0: periodic x; 1: Zou-He inlet x=0, outlet x=Lx-1 */
+  double u_in;          /* inlet velocity (x component)                      */
+  double rho_out;       /* outlet density                                    */
+  int nscalars;         /* passive scalar lattices: 0, 1 or 2                 */
+  double alpha_fluid;   /* scalar diffusivity at theta = 0                    */
+  double alpha_solid;   /* scalar diffusivity at theta = 1 (Sec. 3.2 interp.) */
+  int scalar_inlet;     /* 0: zero; 1: halves (0 for y < Ly/2, else 1; odd
+                           scalars carry the complement)                     */
+  int hot[4];           /* x0, x1, z0, z1 of the T_hot patch on y = 0; x1<=x0
+                           means none                                        */
+  double T_hot;
+  int porosity;         /* lbm_porosity: G(theta) of the Darcy damping        */
+  double porosity_q;
+  int objective;        /* lbm_objective_kind                                */
+  int obj_window;       /* 0: J = F(f^N); K > 0: J = (1/K) sum_{N-K<n<=N} F(f^n) */
+  int nsteps;           /* horizon N of the unsteady problem                 */
+  int precision;        /* lbm_precision of the stored populations           */
+  int ckpt_every;       /* level-1 checkpoint stride (0 = automatic)         */
+  double mem_budget;    /* bytes for stored states (0 = automatic)           */
+} lbm_params;
+
+/* Create a solver.  Defines the lattice, node types, collision (Sec. 3,
+ * Sec. 3.1), porosity parametrisation (Sec. 3.2) and objective.
+ *   out     : receives the handle (owned by the library until lbm_destroy).
+ *   p       : problem description (copied).
+ *   theta   : N floats, host or device; copied.
+ *   flags   : N uint8 node types (LBM_NODE_*), host or device, copied; NULL
+ *             builds the channel geometry described by p.
+ *   stream  : cudaStream_t the handle launches on (NULL = legacy default).
+ * The state starts at f^0 = rest equilibrium (rho = 1, u = 0), scalars 0.
+ * Errors: LBM_ERR_ARG (bad sizes or parameters), LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_create(lbm_handle* out, const lbm_params* p, const float* theta,
+                      const uint8_t* flags, void* stream);
+
+/* Release every device allocation of the handle.  NULL is ignored. */
+void lbm_destroy(lbm_handle h);
+
+/* Message describing the last failure on h (static string if h is NULL). */
+const char* lbm_last_error(lbm_handle h);
+
+/* Replace theta (N floats, host or device) and reset the handle to f^0. */
+lbm_status lbm_set_theta(lbm_handle h, const float* theta);
+
+/* Return to f^0, drop stored states, objective record, adjoint and gradient. */
+lbm_status lbm_reset(lbm_handle h);
+
+/* Advance k primal steps (Eq. normal:iteration, pull form: the fused
+ * kernel gathers f_j(x - e_j) and writes W(f(x)) at x).  Objective terms
+ * c_n F(f^n) are recorded on the way, and states are kept for the adjoint
+ * as the checkpoint schedule requires.  Errors: LBM_ERR_STATE if the
+ * adjoint of this trajectory has started. */
+lbm_status lbm_primal_step(lbm_handle h, int k);
+
+/* Current primal time n (number of steps taken since f^0). */
+int lbm_time(lbm_handle h);
+
+/* J = sum over recorded n of c_n F(f^n) (Eq. objective:function), FP64.
+ * Synchronises the stream.  J_host: host pointer to one double. */
+lbm_status lbm_objective(lbm_handle h, double* J_host);
+
+/* Run k adjoint steps backward in time (Eq. adjoint:iteration, unsteady
+ * form).  The first call starts at the current primal time n = T with
+ * lambda^T = c_T dF/df(f^T) and zeroes the gradient; each step computes
+ * lambda^{n} from lambda^{n+1} and f^n (restored from checkpoints by
+ * recomputation when it was not kept) and adds its theta terms to the FP64
+ * gradient.  Errors: LBM_ERR_STATE when k exceeds the remaining steps. */
+lbm_status lbm_adjoint_step(lbm_handle h, int k);
+
+/* Start the adjoint at the current primal time T with lambda^T = lam (M*N
+ * floats, host or device) instead of the objective source, and zero the
+ * gradient; later lbm_adjoint_step calls continue from there.  Used to
+ * apply the transposed step to an arbitrary vector. */
+lbm_status lbm_adjoint_seed(lbm_handle h, const float* lam);
+
+/* Current adjoint time n (lambda^n is held); -1 before the adjoint starts. */
+int lbm_adjoint_time(lbm_handle h);
+
+/* Full sensitivity solve: reset, nsteps primal steps, nsteps adjoint steps.
+ * Equivalent to lbm_reset + lbm_primal_step(N) + lbm_adjoint_step(N). */
+lbm_status lbm_run(lbm_handle h);
+
+/* Copy dJ/dtheta (N doubles, Eq. adjoint:derivative) into dst, host or
+ * device.  Synchronises the stream when dst is host memory. */
+lbm_status lbm_gradient(lbm_handle h, double* dst);
+
+/* Copy populations of the current primal time into dst (M*N floats, host or
+ * device), as full values f (not deviations).
+ *   which = 0: pre-collision f^n(x) (the paper's state);
+ *   which = 1: post-collision W(f^{n-1}(x)) at x, before streaming. */
+lbm_status lbm_get_populations(lbm_handle h, float* dst, int which);
+
+/* Overwrite the current state with pre-collision populations src (M*N
+ * floats, host or device, full values); drops stored states. */
+lbm_status lbm_set_populations(lbm_handle h, const float* src);
+
+/* Copy lambda^n of the current adjoint time into dst (M*N floats, host or
+ * device).  Errors: LBM_ERR_STATE before the adjoint starts. */
+lbm_status lbm_get_adjoint(lbm_handle h, float* dst);
+
+/* Copy the node-type array (N bytes, host or device). */
+lbm_status lbm_get_flags(lbm_handle h, uint8_t* dst);
+
+/* Count non-finite values in the current state (0 = healthy); synchronises.
+ * Returns LBM_ERR_NONFINITE when the count is positive. */
+lbm_status lbm_check_finite(lbm_handle h, long long* count_host);
+
+/* Sizes: M densities per node and N nodes. */
+lbm_status lbm_sizes(lbm_handle h, int* M, long long* N);
+
+/* Device time of the kernels of the last lbm_primal_step / lbm_adjoint_step
+ * call, measured with CUDA events on the handle's stream (ms; synchronises). */
+lbm_status lbm_last_timing(lbm_handle h, float* primal_ms, float* adjoint_ms);
+
+/* Kernel timing: with enable != 0 every primal, recompute and adjoint
+ * kernel launch is bracketed by CUDA events on the handle's stream. */
+lbm_status lbm_profile(lbm_handle h, int enable);
+
+/* Read and clear the kernel timing record (synchronises): out[8] =
+ * {primal launches, primal ms, recompute launches, recompute ms,
+ *  adjoint launches, adjoint ms, 0, 0}. */
+lbm_status lbm_profile_read(lbm_handle h, double* out);
+
+/* Primal steps recomputed by the checkpoint schedule since the last reset. */
+long long lbm_recompute_steps(lbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALBM_H */

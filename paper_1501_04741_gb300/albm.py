@@ -1,0 +1,290 @@
+"""Python binding of libalbm.so (argument marshalling only).
+
+Every step of the method runs in the library's CUDA kernels; this module
+only converts a :class:`~paper_1501_04741_gb300.inputs.Problem` into the C
+``lbm_params`` struct, passes pointers of torch tensors (device) or numpy
+arrays (host) and the current torch CUDA stream, and turns status codes into
+exceptions.  Importing it loads the library and raises when it is missing;
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .inputs import Problem
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libalbm.so")
+
+LATTICE = {"D2Q9": 0, "D3Q19": 1}
+COLLISION = {"BGK": 0, "MRT": 1}
+PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2}
+POROSITY = {"linear": 0, "power": 1, "ramp": 2}
+OBJECTIVE = {"none": 0, "dissipation": 1, "variance": 2, "heatflux_dp": 3, "mixflux": 4}
+STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
+          4: "LBM_ERR_NONFINITE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
+
+# symbols declared in include/albm.h
+EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_theta", "lbm_reset",
+           "lbm_primal_step", "lbm_time", "lbm_objective", "lbm_adjoint_step",
+           "lbm_adjoint_seed", "lbm_adjoint_time", "lbm_run", "lbm_gradient",
+           "lbm_get_populations", "lbm_set_populations", "lbm_get_adjoint", "lbm_get_flags",
+           "lbm_check_finite", "lbm_sizes", "lbm_last_timing", "lbm_profile",
+           "lbm_profile_read", "lbm_recompute_steps"]
+
+
+class LbmParams(C.Structure):
+    _fields_ = [
+        ("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("collision", C.c_int), ("tau", C.c_double), ("s_other", C.c_double),
+        ("force", C.c_double * 3), ("walls", C.c_int), ("inlet_outlet", C.c_int),
+        ("u_in", C.c_double), ("rho_out", C.c_double), ("nscalars", C.c_int),
+        ("alpha_fluid", C.c_double), ("alpha_solid", C.c_double), ("scalar_inlet", C.c_int),
+        ("hot", C.c_int * 4), ("T_hot", C.c_double), ("porosity", C.c_int),
+        ("porosity_q", C.c_double), ("objective", C.c_int), ("obj_window", C.c_int),
+        ("nsteps", C.c_int), ("precision", C.c_int), ("ckpt_every", C.c_int),
+        ("mem_budget", C.c_double),
+    ]
+
+
+class AlbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libalbm.so once (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libalbm.so not built ({LIB_PATH}); run "
+                               "`python -m paper_1501_04741_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        L.lbm_create.argtypes = [C.POINTER(vp), C.POINTER(LbmParams), vp, vp, vp]
+        L.lbm_destroy.argtypes = [vp]
+        L.lbm_destroy.restype = None
+        L.lbm_last_error.argtypes = [vp]
+        L.lbm_last_error.restype = C.c_char_p
+        for name in ("lbm_set_theta", "lbm_adjoint_seed", "lbm_set_populations"):
+            getattr(L, name).argtypes = [vp, vp]
+        for name in ("lbm_reset", "lbm_run"):
+            getattr(L, name).argtypes = [vp]
+        for name in ("lbm_primal_step", "lbm_adjoint_step", "lbm_profile"):
+            getattr(L, name).argtypes = [vp, i]
+        L.lbm_time.argtypes = [vp]
+        L.lbm_adjoint_time.argtypes = [vp]
+        L.lbm_objective.argtypes = [vp, C.POINTER(d)]
+        L.lbm_gradient.argtypes = [vp, vp]
+        L.lbm_get_populations.argtypes = [vp, vp, i]
+        L.lbm_get_adjoint.argtypes = [vp, vp]
+        L.lbm_get_flags.argtypes = [vp, vp]
+        L.lbm_check_finite.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.lbm_sizes.argtypes = [vp, C.POINTER(i), C.POINTER(C.c_longlong)]
+        L.lbm_last_timing.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+        L.lbm_profile_read.argtypes = [vp, C.POINTER(d)]
+        L.lbm_recompute_steps.argtypes = [vp]
+        L.lbm_recompute_steps.restype = C.c_longlong
+        _lib = L
+    return _lib
+
+
+def make_params(P: Problem, mem_budget: float = 0.0) -> LbmParams:
+    p = LbmParams()
+    p.lattice = LATTICE[P.lattice]
+    p.nx, p.ny, p.nz = (int(v) for v in P.dims)
+    p.collision = COLLISION[P.collision]
+    p.tau = float(P.tau)
+    p.s_other = float(P.s_other)
+    for a in range(3):
+        p.force[a] = float(P.force[a])
+    p.walls = (1 if "y" in P.walls else 0) | (2 if "z" in P.walls else 0)
+    p.inlet_outlet = 1 if P.channel == "inlet_outlet" else 0
+    p.u_in = float(P.u_in)
+    p.rho_out = float(P.rho_out)
+    p.nscalars = int(P.nscalars)
+    p.alpha_fluid = float(P.alpha_fluid)
+    p.alpha_solid = float(P.alpha_solid)
+    p.scalar_inlet = 1 if P.scalar_inlet == "halves" else 0
+    hot = tuple(P.hot) if P.hot else (0, 0, 0, 0)
+    for a in range(4):
+        p.hot[a] = int(hot[a])
+    p.T_hot = float(P.T_hot)
+    p.porosity = POROSITY[P.porosity]
+    p.porosity_q = float(P.porosity_q)
+    p.objective = OBJECTIVE[P.objective]
+    p.obj_window = int(P.obj_window)
+    p.nsteps = int(P.nsteps)
+    p.precision = PRECISION[P.precision]
+    p.ckpt_every = int(P.ckpt_every)
+    p.mem_budget = float(mem_budget)
+    return p
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or a C-contiguous numpy array."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy array must be C-contiguous")
+        return x.ctypes.data
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Solver:
+    """One adjoint-LBM problem on the GPU (a handle of the C library)."""
+
+    def __init__(self, P: Problem, theta, flags=None, stream=None, mem_budget: float = 0.0):
+        import torch
+        self.P = P
+        self._L = lib()
+        self._h = C.c_void_p()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._params = make_params(P, mem_budget)
+        th = self._as_f32(theta)
+        fl = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8)
+        code = self._L.lbm_create(C.byref(self._h), C.byref(self._params), _ptr(th),
+                                  None if fl is None else _ptr(fl), _stream_ptr(self.stream))
+        if code != 0:
+            msg = self._L.lbm_last_error(self._h).decode() if self._h else "lbm_create failed"
+            if self._h:
+                self._L.lbm_destroy(self._h)
+                self._h = C.c_void_p()
+            raise AlbmError(code, msg)
+        M = C.c_int()
+        N = C.c_longlong()
+        self._check(self._L.lbm_sizes(self._h, C.byref(M), C.byref(N)))
+        self.M, self.N = M.value, N.value
+
+    # ---- helpers ---------------------------------------------------------------
+    def _as_f32(self, theta):
+        import torch
+        if isinstance(theta, torch.Tensor):
+            t = theta.detach().to(torch.float32).contiguous().reshape(-1)
+            self._keep = t  # keep alive until the async copy is done
+            return t
+        return np.ascontiguousarray(np.asarray(theta, dtype=np.float32).reshape(-1))
+
+    def _check(self, code):
+        if code != 0:
+            raise AlbmError(code, self._L.lbm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- the C ABI --------------------------------------------------------------
+    def set_theta(self, theta):
+        self._check(self._L.lbm_set_theta(self._h, _ptr(self._as_f32(theta))))
+
+    def reset(self):
+        self._check(self._L.lbm_reset(self._h))
+
+    def primal_step(self, k: int = 1):
+        self._check(self._L.lbm_primal_step(self._h, int(k)))
+
+    def adjoint_step(self, k: int = 1):
+        self._check(self._L.lbm_adjoint_step(self._h, int(k)))
+
+    def adjoint_seed(self, lam):
+        self._check(self._L.lbm_adjoint_seed(self._h, _ptr(lam)))
+
+    def run(self):
+        self._check(self._L.lbm_run(self._h))
+
+    @property
+    def time(self) -> int:
+        return int(self._L.lbm_time(self._h))
+
+    @property
+    def adjoint_time(self) -> int:
+        return int(self._L.lbm_adjoint_time(self._h))
+
+    def objective(self) -> float:
+        J = C.c_double()
+        self._check(self._L.lbm_objective(self._h, C.byref(J)))
+        return J.value
+
+    def gradient(self, out=None):
+        """dJ/dtheta as float64: into ``out`` (tensor or array) or a new device tensor."""
+        import torch
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        self._check(self._L.lbm_gradient(self._h, _ptr(out)))
+        return out
+
+    def populations(self, which: int = 0, out=None):
+        """(M, N) float32 full populations: which=0 pre-collision f^n, 1 post-collision."""
+        import torch
+        if out is None:
+            out = torch.empty((self.M, self.N), dtype=torch.float32, device="cuda")
+        self._check(self._L.lbm_get_populations(self._h, _ptr(out), int(which)))
+        return out
+
+    def set_populations(self, f):
+        self._check(self._L.lbm_set_populations(self._h, _ptr(f)))
+
+    def adjoint(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.M, self.N), dtype=torch.float32, device="cuda")
+        self._check(self._L.lbm_get_adjoint(self._h, _ptr(out)))
+        return out
+
+    def flags(self) -> np.ndarray:
+        out = np.empty(self.N, dtype=np.uint8)
+        self._check(self._L.lbm_get_flags(self._h, _ptr(out)))
+        return out
+
+    def check_finite(self) -> int:
+        c = C.c_longlong()
+        code = self._L.lbm_check_finite(self._h, C.byref(c))
+        if code not in (0, 4):
+            self._check(code)
+        return c.value
+
+    def last_timing(self):
+        a, b = C.c_float(), C.c_float()
+        self._check(self._L.lbm_last_timing(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def profile(self, enable: bool = True):
+        self._check(self._L.lbm_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        out = (C.c_double * 8)()
+        self._check(self._L.lbm_profile_read(self._h, out))
+        v = list(out)
+        return {"primal": (int(v[0]), v[1]), "recompute": (int(v[2]), v[3]),
+                "adjoint": (int(v[4]), v[5])}
+
+    def recompute_steps(self) -> int:
+        return int(self._L.lbm_recompute_steps(self._h))

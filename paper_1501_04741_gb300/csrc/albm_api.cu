@@ -1,0 +1,782 @@
+// Host runtime of libalbm.so: the C ABI declared in include/albm.h.
+//
+// A handle owns the device state of one problem:
+//   * flags (uint8, N), theta (FP32, N), the FP64 gradient (N) and the
+//     per-step objective record (FP64, 2 per step),
+//   * a pool of state buffers B^n (M x N in the storage precision), indexed
+//     by the time n they hold.  The primal kernel writes each new state into
+//     a pool buffer, so keeping a state for the adjoint costs no copy,
+//   * two FP32 adjoint buffers (lambda^{n+1} -> lambda^n ping-pong).
+//
+// Checkpoint schedule of the unsteady adjoint.  The primal pass keeps f^n
+// at every multiple of the level-1 stride K.  When the adjoint needs f^n
+// and it is not kept, the runtime recomputes forward from the latest kept
+// state c < n: if the n - c states fit in the free buffers it keeps them
+// all, otherwise it keeps the densest tail ending at n that fits (and, when
+// even that would leave a head longer than the tail, sub-checkpoints spread
+// over the head); each later request then recomputes a shorter span.  Kept
+// states newer than the adjoint time are released as the adjoint passes
+// them, so the pool never needs more than its budget.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/albm.h"
+#include "albm_kernels.cuh"
+
+using albm::KernelSet;
+using albm::KParams;
+using albm::StepArgs;
+
+struct lbm_ctx {
+  lbm_params p{};
+  KParams kp{};
+  KernelSet ks{};
+  int Q = 0, QS = 0, M = 0;
+  long long N = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  uint8_t* flags = nullptr;
+  float* theta = nullptr;
+  double* grad = nullptr;
+  double* stats = nullptr;          // 2 doubles per step 0..nsteps
+  unsigned long long* counter = nullptr;
+  float* lam[2] = {nullptr, nullptr};
+  int lam_cur = 0;
+  size_t state_bytes = 0;
+  std::vector<void*> bufs;
+  std::vector<int> buf_time;        // time held by each buffer, -1 = free
+  int max_bufs = 3;
+  int ckpt = 1;                     // level-1 stride
+  int t = 0;                        // primal time
+  int t_adj = -1;                   // adjoint time (-1: not started)
+  int n_in = 0, n_out = 0;
+  std::vector<double> c;            // time weights c_n
+  std::vector<uint8_t> flags_host;
+  // profiling: events around launches, grouped by kind
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_used;   // (kind, first event index)
+  size_t ev_next = 0;
+  cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr, t3 = nullptr;
+  float last_primal_ms = 0.f, last_adjoint_ms = 0.f;
+  bool primal_timed = false, adjoint_timed = false;
+  long long recompute_steps = 0;
+  std::string err;
+};
+
+static const char* kNoHandle = "null handle";
+
+#define FAIL(h, code, ...)                                   \
+  do {                                                       \
+    char _b[512];                                            \
+    snprintf(_b, sizeof(_b), __VA_ARGS__);                   \
+    (h)->err = _b;                                           \
+    return code;                                             \
+  } while (0)
+
+#define CK(h, call)                                                               \
+  do {                                                                            \
+    cudaError_t _e = (call);                                                      \
+    if (_e != cudaSuccess) {                                                      \
+      FAIL(h, _e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,       \
+           "%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, __LINE__); \
+    }                                                                             \
+  } while (0)
+
+namespace {
+
+enum { K_PRIMAL = 0, K_RECOMPUTE = 1, K_ADJOINT = 2, K_OTHER = 3 };
+
+int scalar_q(int lattice) { return lattice == LBM_D3Q19 ? 7 : 9; }
+int fluid_q(int lattice) { return lattice == LBM_D3Q19 ? 19 : 9; }
+
+// node types of the channel geometry: inlet/outlet faces, then wall planes
+// (box edges are walls), then the hot patch on the y = 0 plane
+void build_flags(const lbm_params& p, std::vector<uint8_t>& fl) {
+  const long long nx = p.nx, ny = p.ny, nz = p.nz;
+  fl.assign((size_t)(nx * ny * nz), (uint8_t)LBM_NODE_FLUID);
+  for (long long z = 0; z < nz; ++z)
+    for (long long y = 0; y < ny; ++y)
+      for (long long x = 0; x < nx; ++x) {
+        uint8_t t = LBM_NODE_FLUID;
+        if (p.inlet_outlet) {
+          if (x == 0) t = LBM_NODE_INLET;
+          if (x == nx - 1) t = LBM_NODE_OUTLET;
+        }
+        if ((p.walls & 1) && (y == 0 || y == ny - 1)) t = LBM_NODE_WALL;
+        if ((p.walls & 2) && (z == 0 || z == nz - 1)) t = LBM_NODE_WALL;
+        if (p.hot[1] > p.hot[0] && y == 0 && x >= p.hot[0] && x < p.hot[1] && z >= p.hot[2] &&
+            z < p.hot[3])
+          t = LBM_NODE_HOT;
+        fl[(size_t)(x + nx * (y + ny * z))] = t;
+      }
+}
+
+template <class L>
+void mrt_rates(const lbm_params& p, float omega, float* r) {
+  for (int k = 0; k < 19; ++k) r[k] = 0.f;
+  for (int k = 0; k < L::NMOM; ++k) {
+    double D = 0.0;
+    for (int i = 0; i < L::Q; ++i) D += double(L::U(k, i)) * double(L::U(k, i));
+    double s = p.s_other;
+    if (L::conserved(k)) s = 0.0;
+    if (L::stress(k)) s = omega;
+    r[k] = (float)((1.0 - s) / D);
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// buffer pool
+// ---------------------------------------------------------------------------
+static int find_buf(lbm_ctx* h, int t) {
+  for (size_t i = 0; i < h->bufs.size(); ++i)
+    if (h->buf_time[i] == t) return (int)i;
+  return -1;
+}
+
+static int n_kept(lbm_ctx* h) {
+  int n = 0;
+  for (int v : h->buf_time) n += v >= 0;
+  return n;
+}
+
+static lbm_status acquire(lbm_ctx* h, int* out) {
+  for (size_t i = 0; i < h->bufs.size(); ++i)
+    if (h->buf_time[i] == -1) {
+      *out = (int)i;
+      return LBM_OK;
+    }
+  if ((int)h->bufs.size() >= h->max_bufs)
+    FAIL(h, LBM_ERR_OOM, "state pool exhausted (%d buffers of %zu bytes)", h->max_bufs,
+         h->state_bytes);
+  void* p = nullptr;
+  CK(h, cudaMalloc(&p, h->state_bytes));
+  h->bufs.push_back(p);
+  h->buf_time.push_back(-1);
+  *out = (int)h->bufs.size() - 1;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// profiling events
+// ---------------------------------------------------------------------------
+static void prof_begin(lbm_ctx* h, int kind, int* slot) {
+  *slot = -1;
+  if (!h->profile) return;
+  if (h->ev_next + 2 > h->ev_pool.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      h->ev_pool.push_back(e);
+    }
+  }
+  *slot = (int)h->ev_next;
+  h->ev_next += 2;
+  cudaEventRecord(h->ev_pool[*slot], h->stream);
+  h->ev_used.push_back({kind, *slot});
+}
+
+static void prof_end(lbm_ctx* h, int slot) {
+  if (slot >= 0) cudaEventRecord(h->ev_pool[slot + 1], h->stream);
+}
+
+// ---------------------------------------------------------------------------
+// launches
+// ---------------------------------------------------------------------------
+static StepArgs blank_args(lbm_ctx* h) {
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  a.theta = h->theta;
+  a.flags = h->flags;
+  return a;
+}
+
+// one primal step from the state kept at time t (buffer src) into buffer dst
+static lbm_status launch_primal(lbm_ctx* h, int src, int dst, int t, bool record, int kind) {
+  StepArgs a = blank_args(h);
+  a.Bin = h->bufs[src];
+  a.Bout = h->bufs[dst];
+  a.obj = (record && t <= h->p.nsteps && h->c[t] != 0.0) ? h->stats + 2 * (size_t)t : nullptr;
+  int slot;
+  prof_begin(h, kind, &slot);
+  cudaError_t e = h->ks.primal(h->kp, a, h->stream);
+  prof_end(h, slot);
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "primal kernel launch: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+static lbm_status record_final_objective(lbm_ctx* h) {
+  const int t = h->t;
+  if (t > h->p.nsteps || h->c[t] == 0.0 || h->p.objective == LBM_OBJ_NONE) return LBM_OK;
+  StepArgs a = blank_args(h);
+  a.Bin = h->bufs[find_buf(h, t)];
+  a.obj = h->stats + 2 * (size_t)t;
+  cudaError_t e = h->ks.objective(h->kp, a, h->stream);
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "objective kernel launch: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+// make f^n available in the pool (recompute from the latest kept state < n)
+static lbm_status ensure_state(lbm_ctx* h, int n) {
+  if (find_buf(h, n) >= 0) return LBM_OK;
+  int c = -1, cb = -1;
+  for (size_t i = 0; i < h->bufs.size(); ++i)
+    if (h->buf_time[i] >= 0 && h->buf_time[i] < n && h->buf_time[i] > c) {
+      c = h->buf_time[i];
+      cb = (int)i;
+    }
+  if (cb < 0) FAIL(h, LBM_ERR_STATE, "no kept state before time %d", n);
+  const int L = n - c;
+  const int free_now = h->max_bufs - n_kept(h);
+  // states to keep on this pass
+  std::vector<char> keep((size_t)L + 1, 0);  // keep[k] for time c + k
+  if (L <= free_now) {
+    for (int k = 1; k <= L; ++k) keep[k] = 1;
+  } else {
+    const int slots = free_now - 2;  // two scratch buffers for states not kept
+    if (slots < 1) FAIL(h, LBM_ERR_OOM, "state pool too small to recompute (free %d)", free_now);
+    const int head = L - slots;
+    if (head <= slots) {
+      for (int k = L - slots + 1; k <= L; ++k) keep[k] = 1;  // dense tail
+    } else {
+      const int stride = (L + slots - 1) / slots;  // sub-checkpoints
+      for (int k = stride; k < L; k += stride) keep[k] = 1;
+      keep[L] = 1;
+    }
+  }
+  int cur = cb;
+  int scratch[2] = {-1, -1};
+  for (int k = 1; k <= L; ++k) {
+    int dst;
+    if (keep[k]) {
+      lbm_status s = acquire(h, &dst);
+      if (s) return s;
+    } else {
+      // a scratch buffer that is not the source
+      int pick = -1;
+      for (int j = 0; j < 2; ++j)
+        if (scratch[j] >= 0 && scratch[j] != cur) pick = scratch[j];
+      if (pick < 0) {
+        lbm_status s = acquire(h, &pick);
+        if (s) return s;
+        h->buf_time[pick] = -2;  // reserved as scratch
+        if (scratch[0] < 0) scratch[0] = pick; else scratch[1] = pick;
+      }
+      dst = pick;
+    }
+    lbm_status s = launch_primal(h, cur, dst, c + k - 1, false, K_RECOMPUTE);
+    if (s) return s;
+    h->recompute_steps++;
+    if (keep[k]) h->buf_time[dst] = c + k;
+    else h->buf_time[dst] = -2;
+    cur = dst;
+  }
+  for (int j = 0; j < 2; ++j)
+    if (scratch[j] >= 0 && h->buf_time[scratch[j]] == -2) h->buf_time[scratch[j]] = -1;
+  return LBM_OK;
+}
+
+static lbm_status launch_adjoint(lbm_ctx* h, int n, int has_next) {
+  StepArgs a = blank_args(h);
+  a.Bin = h->bufs[find_buf(h, n)];
+  a.lam_in = h->lam[h->lam_cur];
+  a.lam_out = h->lam[1 - h->lam_cur];
+  a.grad = h->grad;
+  a.ws = (float)h->c[n];
+  a.stat_n = (h->p.objective == LBM_OBJ_VARIANCE && h->c[n] != 0.0) ? h->stats + 2 * (size_t)n
+                                                                     : nullptr;
+  a.has_next = has_next;
+  int slot;
+  prof_begin(h, K_ADJOINT, &slot);
+  cudaError_t e = h->ks.adjoint(h->kp, a, h->stream);
+  prof_end(h, slot);
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "adjoint kernel launch: %s", cudaGetErrorString(e));
+  h->lam_cur = 1 - h->lam_cur;
+  return LBM_OK;
+}
+
+static lbm_status do_reset(lbm_ctx* h) {
+  for (auto& t : h->buf_time) t = -1;
+  int b;
+  lbm_status s = acquire(h, &b);
+  if (s) return s;
+  CK(h, cudaMemsetAsync(h->bufs[b], 0, h->state_bytes, h->stream));  // f^0 = rest state
+  h->buf_time[b] = 0;
+  h->t = 0;
+  h->t_adj = -1;
+  h->recompute_steps = 0;
+  CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * 2 * (size_t)(h->p.nsteps + 1), h->stream));
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : kNoHandle; }
+
+lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
+                      const uint8_t* flags, void* stream) {
+  if (!out || !pp) return LBM_ERR_ARG;
+  *out = nullptr;
+  lbm_ctx* h = new lbm_ctx();
+  h->p = *pp;
+  const lbm_params& p = h->p;
+  auto bad = [&](const char* msg) {
+    h->err = msg;
+    return LBM_ERR_ARG;
+  };
+  lbm_status st = LBM_OK;
+  if (p.lattice != LBM_D2Q9 && p.lattice != LBM_D3Q19) st = bad("lattice must be D2Q9 or D3Q19");
+  else if (p.nx < 1 || p.ny < 1 || p.nz < 1) st = bad("lattice sizes must be positive");
+  else if (p.lattice == LBM_D2Q9 && p.nz != 1) st = bad("D2Q9 needs nz == 1");
+  else if (p.lattice == LBM_D2Q9 && p.force[2] != 0.0) st = bad("D2Q9 needs force[2] == 0");
+  else if (p.collision != LBM_BGK && p.collision != LBM_MRT) st = bad("collision must be BGK or MRT");
+  else if (!(p.tau > 0.5)) st = bad("tau must exceed 1/2");
+  else if (p.nscalars < 0 || p.nscalars > (p.lattice == LBM_D3Q19 ? 2 : 1))
+    st = bad("nscalars out of range (D3Q19: 0..2, D2Q9: 0..1)");
+  else if (p.precision < 0 || p.precision > 2) st = bad("precision must be FP32, BF16 or FP16");
+  else if (p.nsteps < 0) st = bad("nsteps must be >= 0");
+  else if (p.obj_window < 0 || p.obj_window > p.nsteps + 1) st = bad("obj_window out of range");
+  else if (p.objective < 0 || p.objective > 4) st = bad("unknown objective");
+  else if (p.objective >= LBM_OBJ_VARIANCE && (p.nscalars < 1 || !p.inlet_outlet))
+    st = bad("outlet objectives need a scalar lattice and inlet_outlet");
+  else if (p.porosity < 0 || p.porosity > 2) st = bad("unknown porosity law");
+  else if (p.porosity == LBM_POR_POWER && p.porosity_q < 1.0) st = bad("power porosity needs q >= 1");
+  else if (p.inlet_outlet && (p.nx < 3 || !(p.u_in < 1.0) || !(p.rho_out > 0.0)))
+    st = bad("inlet_outlet needs nx >= 3, u_in < 1 and rho_out > 0");
+  else if (!theta) st = bad("theta must not be NULL");
+  if (st) {
+    *out = h;  // so that lbm_last_error can report; caller destroys
+    return st;
+  }
+  h->Q = fluid_q(p.lattice);
+  h->QS = scalar_q(p.lattice);
+  h->M = h->Q + p.nscalars * h->QS;
+  h->N = (long long)p.nx * p.ny * p.nz;
+  h->stream = (cudaStream_t)stream;
+  bool ok = p.lattice == LBM_D2Q9
+                ? albm::kernels_d2q9(p.collision, p.nscalars, p.precision, &h->ks)
+                : (p.collision == LBM_MRT ? albm::kernels_d3q19_mrt(p.nscalars, p.precision, &h->ks)
+                                          : albm::kernels_d3q19_bgk(p.nscalars, p.precision, &h->ks));
+  if (!ok) {
+    *out = h;
+    h->err = "no kernel for this lattice/collision/scalars/precision";
+    return LBM_ERR_ARG;
+  }
+  // kernel constants
+  KParams& k = h->kp;
+  k.nx = p.nx;
+  k.ny = p.ny;
+  k.nz = p.nz;
+  k.nscal = p.nscalars;
+  k.N = h->N;
+  const double omega = 1.0 / p.tau;
+  k.omega = (float)omega;
+  k.one_m_omega = (float)(1.0 - omega);
+  k.nu = (float)((p.tau - 0.5) / 3.0);
+  k.gx = (float)p.force[0];
+  k.gy = (float)p.force[1];
+  k.gz = (float)p.force[2];
+  k.u_in = (float)p.u_in;
+  k.inv_1m_uin = (float)(1.0 / (1.0 - p.u_in));
+  k.rho_out = (float)p.rho_out;
+  k.drho_out = (float)(p.rho_out - 1.0);
+  k.one_m_rho_out = (float)(1.0 - p.rho_out);
+  k.alpha_f = (float)p.alpha_fluid;
+  k.alpha_s = (float)p.alpha_solid;
+  k.porosity = p.porosity;
+  k.por_q = (float)p.porosity_q;
+  k.scalar_inlet = p.scalar_inlet;
+  k.T_hot = (float)p.T_hot;
+  k.objective = p.objective;
+  if (p.collision == LBM_MRT) {
+    if (p.lattice == LBM_D3Q19) mrt_rates<albm::D3Q19>(p, (float)omega, k.mrt_r);
+    else mrt_rates<albm::D2Q9>(p, (float)omega, k.mrt_r);
+  }
+  h->state_bytes = (size_t)h->M * (size_t)h->N * (size_t)h->ks.storage_bytes;
+  // time weights c_n of J = sum_n c_n F(f^n)
+  h->c.assign((size_t)p.nsteps + 1, 0.0);
+  if (p.objective != LBM_OBJ_NONE) {
+    if (p.obj_window <= 0) h->c[p.nsteps] = 1.0;
+    else
+      for (int n = std::max(p.nsteps - p.obj_window + 1, 0); n <= p.nsteps; ++n)
+        h->c[n] = 1.0 / p.obj_window;
+  }
+  auto fail = [&](lbm_status s) {
+    *out = h;
+    return s;
+  };
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    h->err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    return fail(LBM_ERR_CUDA);
+  }
+  // device arrays
+#define CKC(call)                                                            \
+  do {                                                                       \
+    cudaError_t _e = (call);                                                 \
+    if (_e != cudaSuccess) {                                                 \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(_e);           \
+      return fail(_e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA); \
+    }                                                                        \
+  } while (0)
+  CKC(cudaMalloc(&h->flags, (size_t)h->N));
+  CKC(cudaMalloc(&h->theta, sizeof(float) * (size_t)h->N));
+  CKC(cudaMalloc(&h->grad, sizeof(double) * (size_t)h->N));
+  CKC(cudaMalloc(&h->stats, sizeof(double) * 2 * (size_t)(p.nsteps + 1)));
+  CKC(cudaMalloc(&h->counter, sizeof(unsigned long long)));
+  CKC(cudaMalloc(&h->lam[0], sizeof(float) * (size_t)h->M * (size_t)h->N));
+  CKC(cudaMalloc(&h->lam[1], sizeof(float) * (size_t)h->M * (size_t)h->N));
+  CKC(cudaMemsetAsync(h->grad, 0, sizeof(double) * (size_t)h->N, h->stream));
+  CKC(cudaMemcpyAsync(h->theta, theta, sizeof(float) * (size_t)h->N, cudaMemcpyDefault, h->stream));
+  if (flags) {
+    h->flags_host.resize((size_t)h->N);
+    CKC(cudaMemcpyAsync(h->flags_host.data(), flags, (size_t)h->N, cudaMemcpyDefault, h->stream));
+    CKC(cudaStreamSynchronize(h->stream));
+    for (uint8_t v : h->flags_host)
+      if (v > LBM_NODE_HOT) {
+        h->err = "flags hold an unknown node type";
+        return fail(LBM_ERR_ARG);
+      }
+  } else {
+    build_flags(p, h->flags_host);
+  }
+  CKC(cudaMemcpyAsync(h->flags, h->flags_host.data(), (size_t)h->N, cudaMemcpyHostToDevice,
+                      h->stream));
+  for (uint8_t v : h->flags_host) {
+    h->n_in += v == LBM_NODE_INLET;
+    h->n_out += v == LBM_NODE_OUTLET;
+  }
+  k.inv_A_in = h->n_in ? 1.0f / (float)h->n_in : 0.f;
+  k.inv_A_out = h->n_out ? 1.0f / (float)h->n_out : 0.f;
+  // state pool budget
+  double budget = p.mem_budget;
+  if (budget <= 0) {
+    size_t fr = 0, tot = 0;
+    CKC(cudaMemGetInfo(&fr, &tot));
+    budget = 0.6 * (double)fr;
+  }
+  h->max_bufs = (int)std::max(3.0, std::floor(budget / (double)h->state_bytes));
+  // level-1 checkpoint stride: given, or every state if all fit, else
+  // spread over half of the pool
+  if (p.ckpt_every > 0) h->ckpt = p.ckpt_every;
+  else if (p.nsteps + 2 <= h->max_bufs) h->ckpt = 1;
+  else h->ckpt = std::max(1, (p.nsteps + h->max_bufs / 2 - 1) / std::max(1, h->max_bufs / 2));
+  CKC(cudaEventCreate(&h->t0));
+  CKC(cudaEventCreate(&h->t1));
+  CKC(cudaEventCreate(&h->t2));
+  CKC(cudaEventCreate(&h->t3));
+#undef CKC
+  lbm_status s = do_reset(h);
+  if (s) return fail(s);
+  *out = h;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* b : h->bufs) cudaFree(b);
+  cudaFree(h->flags);
+  cudaFree(h->theta);
+  cudaFree(h->grad);
+  cudaFree(h->stats);
+  cudaFree(h->counter);
+  cudaFree(h->lam[0]);
+  cudaFree(h->lam[1]);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->t0) cudaEventDestroy(h->t0);
+  if (h->t1) cudaEventDestroy(h->t1);
+  if (h->t2) cudaEventDestroy(h->t2);
+  if (h->t3) cudaEventDestroy(h->t3);
+  delete h;
+}
+
+lbm_status lbm_reset(lbm_handle h) {
+  if (!h) return LBM_ERR_ARG;
+  return do_reset(h);
+}
+
+lbm_status lbm_set_theta(lbm_handle h, const float* theta) {
+  if (!h || !theta) return LBM_ERR_ARG;
+  CK(h, cudaMemcpyAsync(h->theta, theta, sizeof(float) * (size_t)h->N, cudaMemcpyDefault,
+                        h->stream));
+  return do_reset(h);
+}
+
+int lbm_time(lbm_handle h) { return h ? h->t : -1; }
+int lbm_adjoint_time(lbm_handle h) { return h ? h->t_adj : -1; }
+
+lbm_status lbm_primal_step(lbm_handle h, int k) {
+  if (!h) return LBM_ERR_ARG;
+  if (k < 0 || h->t + k > h->p.nsteps)
+    FAIL(h, LBM_ERR_ARG, "primal steps %d from time %d exceed the horizon %d", k, h->t,
+         h->p.nsteps);
+  if (h->t_adj >= 0) FAIL(h, LBM_ERR_STATE, "the adjoint of this trajectory has started; reset first");
+  CK(h, cudaEventRecord(h->t0, h->stream));
+  for (int i = 0; i < k; ++i) {
+    const int src = find_buf(h, h->t);
+    int dst;
+    lbm_status s = acquire(h, &dst);
+    if (s) return s;
+    s = launch_primal(h, src, dst, h->t, true, K_PRIMAL);
+    if (s) return s;
+    h->buf_time[dst] = h->t + 1;
+    if (h->t % h->ckpt != 0) h->buf_time[src] = -1;  // not a checkpoint
+    h->t += 1;
+  }
+  if (k > 0 && h->t == h->p.nsteps) {
+    lbm_status s = record_final_objective(h);
+    if (s) return s;
+  }
+  CK(h, cudaEventRecord(h->t1, h->stream));
+  h->primal_timed = k > 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_objective(lbm_handle h, double* J) {
+  if (!h || !J) return LBM_ERR_ARG;
+  std::vector<double> st(2 * (size_t)(h->p.nsteps + 1));
+  CK(h, cudaMemcpyAsync(st.data(), h->stats, sizeof(double) * st.size(), cudaMemcpyDeviceToHost,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  double acc = 0.0;
+  const double A = h->n_out > 0 ? (double)h->n_out : 1.0;
+  for (int n = 0; n <= std::min(h->t, h->p.nsteps); ++n) {
+    if (h->c[n] == 0.0) continue;
+    double Fn;
+    switch (h->p.objective) {
+      case LBM_OBJ_VARIANCE: {
+        const double m = st[2 * n] / A;
+        Fn = st[2 * n + 1] / A - m * m;
+        break;
+      }
+      case LBM_OBJ_HEATFLUX_DP:
+        Fn = st[2 * n] + 0.1 * h->p.rho_out / 3.0;
+        break;
+      default:
+        Fn = st[2 * n];
+    }
+    acc += h->c[n] * Fn;
+  }
+  *J = acc;
+  return LBM_OK;
+}
+
+static lbm_status adjoint_start(lbm_handle h) {
+  CK(h, cudaMemsetAsync(h->grad, 0, sizeof(double) * (size_t)h->N, h->stream));
+  h->lam_cur = 0;
+  h->t_adj = h->t;
+  // lambda^T = c_T dF/df(f^T): the adjoint kernel without the next state
+  return launch_adjoint(h, h->t, 0);
+}
+
+lbm_status lbm_adjoint_step(lbm_handle h, int k) {
+  if (!h) return LBM_ERR_ARG;
+  if (k < 0) FAIL(h, LBM_ERR_ARG, "negative step count");
+  CK(h, cudaEventRecord(h->t2, h->stream));
+  if (h->t_adj < 0) {
+    lbm_status s = adjoint_start(h);
+    if (s) return s;
+  }
+  if (k > h->t_adj) FAIL(h, LBM_ERR_STATE, "%d adjoint steps requested, %d remain", k, h->t_adj);
+  for (int i = 0; i < k; ++i) {
+    const int n = h->t_adj - 1;
+    // states newer than n are no longer needed
+    for (size_t b = 0; b < h->bufs.size(); ++b)
+      if (h->buf_time[b] > n) h->buf_time[b] = -1;
+    lbm_status s = ensure_state(h, n);
+    if (s) return s;
+    s = launch_adjoint(h, n, 1);
+    if (s) return s;
+    h->t_adj = n;
+  }
+  CK(h, cudaEventRecord(h->t3, h->stream));
+  h->adjoint_timed = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_adjoint_seed(lbm_handle h, const float* lam) {
+  if (!h || !lam) return LBM_ERR_ARG;
+  if (find_buf(h, h->t) < 0) FAIL(h, LBM_ERR_STATE, "current state not held");
+  CK(h, cudaMemsetAsync(h->grad, 0, sizeof(double) * (size_t)h->N, h->stream));
+  h->lam_cur = 0;
+  h->t_adj = h->t;
+  CK(h, cudaMemcpyAsync(h->lam[0], lam, sizeof(float) * (size_t)h->M * (size_t)h->N,
+                        cudaMemcpyDefault, h->stream));
+  if (!is_device_ptr(lam)) CK(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_profile(lbm_handle h, int enable) {
+  if (!h) return LBM_ERR_ARG;
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->profile = enable != 0;
+  h->ev_used.clear();
+  h->ev_next = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_handle h, double* out) {
+  if (!h || !out) return LBM_ERR_ARG;
+  CK(h, cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < 8; ++i) out[i] = 0.0;
+  for (auto& u : h->ev_used) {
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, h->ev_pool[u.second], h->ev_pool[u.second + 1]));
+    out[2 * u.first] += 1.0;
+    out[2 * u.first + 1] += ms;
+  }
+  h->ev_used.clear();
+  h->ev_next = 0;
+  return LBM_OK;
+}
+
+long long lbm_recompute_steps(lbm_handle h) { return h ? h->recompute_steps : -1; }
+
+lbm_status lbm_run(lbm_handle h) {
+  if (!h) return LBM_ERR_ARG;
+  lbm_status s = do_reset(h);
+  if (s) return s;
+  s = lbm_primal_step(h, h->p.nsteps);
+  if (s) return s;
+  return lbm_adjoint_step(h, h->p.nsteps);
+}
+
+lbm_status lbm_gradient(lbm_handle h, double* dst) {
+  if (!h || !dst) return LBM_ERR_ARG;
+  if (h->t_adj < 0) FAIL(h, LBM_ERR_STATE, "no adjoint has run");
+  CK(h, cudaMemcpyAsync(dst, h->grad, sizeof(double) * (size_t)h->N, cudaMemcpyDefault, h->stream));
+  if (!is_device_ptr(dst)) CK(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_handle h, float* dst, int which) {
+  if (!h || !dst) return LBM_ERR_ARG;
+  const int b = find_buf(h, h->t);
+  if (b < 0) FAIL(h, LBM_ERR_STATE, "current state not held");
+  const bool dev = is_device_ptr(dst);
+  float* out = dst;
+  if (!dev) CK(h, cudaMalloc(&out, sizeof(float) * (size_t)h->M * (size_t)h->N));
+  StepArgs a = blank_args(h);
+  a.Bin = h->bufs[b];
+  a.fout = out;
+  a.post = which;
+  cudaError_t e = h->ks.exportf(h->kp, a, h->stream);
+  if (e == cudaSuccess && !dev)
+    e = cudaMemcpyAsync(dst, out, sizeof(float) * (size_t)h->M * (size_t)h->N,
+                        cudaMemcpyDeviceToHost, h->stream);
+  if (!dev) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(out);
+  }
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "export: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_handle h, const float* src) {
+  if (!h || !src) return LBM_ERR_ARG;
+  for (auto& t : h->buf_time) t = -1;
+  int b;
+  lbm_status s = acquire(h, &b);
+  if (s) return s;
+  const bool dev = is_device_ptr(src);
+  const float* in = src;
+  float* tmp = nullptr;
+  if (!dev) {
+    CK(h, cudaMalloc(&tmp, sizeof(float) * (size_t)h->M * (size_t)h->N));
+    CK(h, cudaMemcpyAsync(tmp, src, sizeof(float) * (size_t)h->M * (size_t)h->N,
+                          cudaMemcpyHostToDevice, h->stream));
+    in = tmp;
+  }
+  StepArgs a = blank_args(h);
+  a.fin = in;
+  a.Bout = h->bufs[b];
+  cudaError_t e = h->ks.importf(h->kp, a, h->stream);
+  if (tmp) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+  }
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "import: %s", cudaGetErrorString(e));
+  h->buf_time[b] = 0;
+  h->t = 0;
+  h->t_adj = -1;
+  CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * 2 * (size_t)(h->p.nsteps + 1), h->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_adjoint(lbm_handle h, float* dst) {
+  if (!h || !dst) return LBM_ERR_ARG;
+  if (h->t_adj < 0) FAIL(h, LBM_ERR_STATE, "no adjoint has run");
+  CK(h, cudaMemcpyAsync(dst, h->lam[h->lam_cur], sizeof(float) * (size_t)h->M * (size_t)h->N,
+                        cudaMemcpyDefault, h->stream));
+  if (!is_device_ptr(dst)) CK(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_flags(lbm_handle h, uint8_t* dst) {
+  if (!h || !dst) return LBM_ERR_ARG;
+  CK(h, cudaMemcpyAsync(dst, h->flags, (size_t)h->N, cudaMemcpyDefault, h->stream));
+  if (!is_device_ptr(dst)) CK(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_check_finite(lbm_handle h, long long* count) {
+  if (!h || !count) return LBM_ERR_ARG;
+  const int b = find_buf(h, h->t);
+  if (b < 0) FAIL(h, LBM_ERR_STATE, "current state not held");
+  CK(h, cudaMemsetAsync(h->counter, 0, sizeof(unsigned long long), h->stream));
+  StepArgs a = blank_args(h);
+  a.Bin = h->bufs[b];
+  a.count = h->counter;
+  cudaError_t e = h->ks.nonfinite(h->kp, a, h->M, h->stream);
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "nonfinite: %s", cudaGetErrorString(e));
+  unsigned long long c = 0;
+  CK(h, cudaMemcpyAsync(&c, h->counter, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  *count = (long long)c;
+  if (c) FAIL(h, LBM_ERR_NONFINITE, "%llu non-finite values in the state at time %d", c, h->t);
+  return LBM_OK;
+}
+
+lbm_status lbm_sizes(lbm_handle h, int* M, long long* N) {
+  if (!h) return LBM_ERR_ARG;
+  if (M) *M = h->M;
+  if (N) *N = h->N;
+  return LBM_OK;
+}
+
+lbm_status lbm_last_timing(lbm_handle h, float* primal_ms, float* adjoint_ms) {
+  if (!h) return LBM_ERR_ARG;
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (primal_ms) {
+    *primal_ms = 0.f;
+    if (h->primal_timed) CK(h, cudaEventElapsedTime(primal_ms, h->t0, h->t1));
+  }
+  if (adjoint_ms) {
+    *adjoint_ms = 0.f;
+    if (h->adjoint_timed) CK(h, cudaEventElapsedTime(adjoint_ms, h->t2, h->t3));
+  }
+  return LBM_OK;
+}
+
+}  // extern "C"

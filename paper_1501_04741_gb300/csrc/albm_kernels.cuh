@@ -1,0 +1,359 @@
+// Fused pull-scheme kernels of the primal and adjoint steps.
+//
+// State buffer B (storage type S, M rows of N, deviations for the fluid):
+// B^n_j(x) = W_j(f^{n-1}(x)), so the pre-collision state of Eq.
+// "normal:iteration" is f^n_j(x) = w_j + B^n_j(x - e_j) (periodic shifts).
+// One primal step gathers f^n(x) from the 19 (or 9) neighbours, applies the
+// node operator W^x and writes B^{n+1}(x) at x: the reads are the only
+// misaligned accesses, the writes are fully coalesced.
+//
+// Adjoint (Eqs. "adjoint:iteration" and "adjoint:operator", unsteady form):
+// lambda^n_k(x) = sum_j lambda^{n+1}_j(x + e_j) dW^x_j/df_k(f^n(x)) + c_n dF^x/df_k,
+// so the kernel gathers lambda^{n+1} from x + e_j, gathers f^n from B^n at
+// x - e_j, applies the transposed node operator in registers and writes
+// lambda^n(x) at x; the theta terms (Eq. "adjoint:derivative") are added to
+// the FP64 gradient of the node.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "albm_node.cuh"
+
+namespace albm {
+
+// ---- storage conversions -------------------------------------------------
+__device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ void st(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+
+// ---- periodic neighbourhood of one node ----------------------------------
+struct Geo {
+  long long idx;
+  int x, y, z;
+  long long oxm, oxp, oym, oyp, ozm, ozp;  // index offsets to x-1, x+1, ...
+  __device__ __forceinline__ long long off(int sx, int sy, int sz) const {
+    long long o = 0;
+    if (sx > 0) o += oxp;
+    if (sx < 0) o += oxm;
+    if (sy > 0) o += oyp;
+    if (sy < 0) o += oym;
+    if (sz > 0) o += ozp;
+    if (sz < 0) o += ozm;
+    return o;
+  }
+};
+
+__device__ __forceinline__ Geo make_geo(const KParams& P, long long idx) {
+  Geo g;
+  g.idx = idx;
+  const long long r = idx / P.nx;
+  g.x = (int)(idx - r * P.nx);
+  g.z = (int)(r / P.ny);
+  g.y = (int)(r - (long long)g.z * P.ny);
+  const long long sxy = (long long)P.nx * P.ny;
+  g.oxm = (g.x == 0) ? (P.nx - 1) : -1;
+  g.oxp = (g.x == P.nx - 1) ? -(P.nx - 1) : 1;
+  g.oym = ((g.y == 0) ? (P.ny - 1) : -1) * (long long)P.nx;
+  g.oyp = ((g.y == P.ny - 1) ? -(P.ny - 1) : 1) * (long long)P.nx;
+  g.ozm = ((g.z == 0) ? (P.nz - 1) : -1) * sxy;
+  g.ozp = ((g.z == P.nz - 1) ? -(P.nz - 1) : 1) * sxy;
+  return g;
+}
+
+// ---- block reduction of two doubles into global accumulators -------------
+__device__ __forceinline__ void block_sum2(double a, double b, double* out) {
+  __shared__ double sa[32], sb[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sa[wid] = a;
+    sb[wid] = b;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    a = lane < nw ? sa[lane] : 0.0;
+    b = lane < nw ? sb[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      if (a != 0.0) atomicAdd(out, a);
+      if (b != 0.0) atomicAdd(out + 1, b);
+    }
+  }
+}
+
+template <class L, int NS, class S>
+struct Gather {
+  using LS = typename ScalarOf<L>::type;
+  static constexpr int Q = L::Q, QS = LS::Q;
+  static constexpr int NSA = NS > 0 ? NS : 1;
+  // f^n(x) from B^n: d_j = B_j(x - e_j), g_j = B_{Q+s QS+j}(x - e_j)
+  __device__ static __forceinline__ void pre(const Geo& geo, long long N, const S* __restrict__ B,
+                                             float* d, float (*g)[QS]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      d[i] = ld(B + (long long)i * N + geo.idx + geo.off(-L::ex(i), -L::ey(i), -L::ez(i)));
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < QS; ++i)
+        g[s][i] = ld(B + (long long)(Q + s * QS + i) * N + geo.idx +
+                     geo.off(-LS::ex(i), -LS::ey(i), -LS::ez(i)));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// primal step: B^{n+1}(x) = W^x(f^n(x)); optional objective terms of f^n
+// ---------------------------------------------------------------------------
+template <class L, int NS, bool MRT, class S>
+__global__ void __launch_bounds__(256) primal_kernel(KParams P, const S* __restrict__ Bin,
+                                                     S* __restrict__ Bout,
+                                                     const float* __restrict__ theta,
+                                                     const uint8_t* __restrict__ flags,
+                                                     double* __restrict__ obj) {
+  using Ops = NodeOps<L, NS, MRT>;
+  constexpr int Q = Ops::Q, QS = Ops::QS, NSA = Ops::NSA;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double o1 = 0.0, o2 = 0.0;
+  if (idx < P.N) {
+    const Geo geo = make_geo(P, idx);
+    float d[Q], g[NSA][QS];
+    Gather<L, NS, S>::pre(geo, P.N, Bin, d, g);
+    const uint8_t type = flags[idx];
+    const float th = theta[idx];
+    Ops::forward(P, type, th, geo.y, d, g, obj != nullptr, o1, o2);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, d[i]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < QS; ++i) st(Bout + (long long)(Q + s * QS + i) * P.N + idx, g[s][i]);
+  }
+  if (obj != nullptr) block_sum2(o1, o2, obj);
+}
+
+// objective terms of f^n only (no state write), used for F(f^N)
+template <class L, int NS, bool MRT, class S>
+__global__ void __launch_bounds__(256) objective_kernel(KParams P, const S* __restrict__ Bin,
+                                                        const float* __restrict__ theta,
+                                                        const uint8_t* __restrict__ flags,
+                                                        double* __restrict__ obj) {
+  using Ops = NodeOps<L, NS, MRT>;
+  constexpr int Q = Ops::Q, QS = Ops::QS, NSA = Ops::NSA;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double o1 = 0.0, o2 = 0.0;
+  if (idx < P.N) {
+    const uint8_t type = flags[idx];
+    const bool relevant = (P.objective == OBJ_DISSIPATION) ? (type == FLUID)
+                                                           : (type == OUTLET || type == INLET);
+    if (relevant) {
+      const Geo geo = make_geo(P, idx);
+      float d[Q], g[NSA][QS];
+      Gather<L, NS, S>::pre(geo, P.N, Bin, d, g);
+      Ops::forward(P, type, theta[idx], geo.y, d, g, true, o1, o2);
+    }
+  }
+  block_sum2(o1, o2, obj);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint step: lambda^n(x) from lambda^{n+1}(x + e_j) and f^n(x)
+// ---------------------------------------------------------------------------
+template <class L, int NS, bool MRT, class S>
+__global__ void __launch_bounds__(256) adjoint_kernel(KParams P, const float* __restrict__ lam_in,
+                                                      const S* __restrict__ Bn,
+                                                      float* __restrict__ lam_out,
+                                                      const float* __restrict__ theta,
+                                                      const uint8_t* __restrict__ flags,
+                                                      double* __restrict__ grad, float ws,
+                                                      const double* __restrict__ stat_n,
+                                                      int has_next) {
+  using Ops = NodeOps<L, NS, MRT>;
+  using LS = typename Ops::LS;
+  constexpr int Q = Ops::Q, QS = Ops::QS, NSA = Ops::NSA;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.N) return;
+  const Geo geo = make_geo(P, idx);
+  float d[Q], g[NSA][QS], a[Q], b[NSA][QS];
+  Gather<L, NS, S>::pre(geo, P.N, Bn, d, g);
+  if (has_next) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      a[i] = __ldg(lam_in + (long long)i * P.N + idx + geo.off(L::ex(i), L::ey(i), L::ez(i)));
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < QS; ++i)
+        b[s][i] = __ldg(lam_in + (long long)(Q + s * QS + i) * P.N + idx +
+                        geo.off(LS::ex(i), LS::ey(i), LS::ez(i)));
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) a[i] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < NSA; ++s)
+#pragma unroll
+      for (int i = 0; i < QS; ++i) b[s][i] = 0.0f;
+  }
+  const uint8_t type = flags[idx];
+  // outlet mean of scalar 0 at this step (variance objective)
+  const float cbar = stat_n != nullptr ? (float)(stat_n[0] * (double)P.inv_A_out) : 0.0f;
+  float lam[Q], lamg[NSA][QS], dth;
+  Ops::reverse(P, type, theta[idx], geo.y, d, g, a, b, ws, cbar, lam, lamg, dth);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) lam_out[(long long)i * P.N + idx] = lam[i];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int i = 0; i < QS; ++i) lam_out[(long long)(Q + s * QS + i) * P.N + idx] = lamg[s][i];
+  if (type == FLUID || type == INLET || type == OUTLET) grad[idx] += (double)dth;
+}
+
+// ---------------------------------------------------------------------------
+// state import / export (full values, FP32) and health check
+// ---------------------------------------------------------------------------
+template <class L, int NS, class S>
+__global__ void export_kernel(KParams P, const S* __restrict__ B, float* __restrict__ out, int post) {
+  using LS = typename ScalarOf<L>::type;
+  constexpr int Q = L::Q, QS = LS::Q;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.N) return;
+  const Geo geo = make_geo(P, idx);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const long long src = post ? idx : idx + geo.off(-L::ex(i), -L::ey(i), -L::ez(i));
+    out[(long long)i * P.N + idx] = L::w(i) + ld(B + (long long)i * P.N + src);
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int i = 0; i < QS; ++i) {
+      const long long m = Q + s * QS + i;
+      const long long src = post ? idx : idx + geo.off(-LS::ex(i), -LS::ey(i), -LS::ez(i));
+      out[m * P.N + idx] = ld(B + m * P.N + src);
+    }
+}
+
+// B_j(x) = f_j(x + e_j) - w_j, so that the gather of the next step sees f
+template <class L, int NS, class S>
+__global__ void import_kernel(KParams P, const float* __restrict__ in, S* __restrict__ B) {
+  using LS = typename ScalarOf<L>::type;
+  constexpr int Q = L::Q, QS = LS::Q;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.N) return;
+  const Geo geo = make_geo(P, idx);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const long long src = idx + geo.off(L::ex(i), L::ey(i), L::ez(i));
+    st(B + (long long)i * P.N + idx, __ldg(in + (long long)i * P.N + src) - L::w(i));
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int i = 0; i < QS; ++i) {
+      const long long m = Q + s * QS + i;
+      const long long src = idx + geo.off(LS::ex(i), LS::ey(i), LS::ez(i));
+      st(B + m * P.N + idx, __ldg(in + m * P.N + src));
+    }
+}
+
+template <class S>
+__global__ void nonfinite_kernel(const S* __restrict__ B, long long n, unsigned long long* count) {
+  unsigned long long c = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float v = ld(B + i);
+    if (!isfinite(v)) ++c;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers, one set per (lattice, collision, scalars, storage)
+// ---------------------------------------------------------------------------
+struct StepArgs {
+  const void* Bin;
+  void* Bout;
+  const float* theta;
+  const uint8_t* flags;
+  double* obj;
+  const float* lam_in;
+  float* lam_out;
+  double* grad;
+  float ws;
+  const double* stat_n;
+  int has_next;
+  const float* fin;
+  float* fout;
+  int post;
+  unsigned long long* count;
+};
+
+struct KernelSet {
+  cudaError_t (*primal)(const KParams&, const StepArgs&, cudaStream_t);
+  cudaError_t (*objective)(const KParams&, const StepArgs&, cudaStream_t);
+  cudaError_t (*adjoint)(const KParams&, const StepArgs&, cudaStream_t);
+  cudaError_t (*exportf)(const KParams&, const StepArgs&, cudaStream_t);
+  cudaError_t (*importf)(const KParams&, const StepArgs&, cudaStream_t);
+  cudaError_t (*nonfinite)(const KParams&, const StepArgs&, int M, cudaStream_t);
+  int storage_bytes;
+};
+
+constexpr int kBlock = 256;
+
+template <class L, int NS, bool MRT, class S>
+struct Launch {
+  static unsigned blocks(const KParams& P) { return (unsigned)((P.N + kBlock - 1) / kBlock); }
+  static cudaError_t primal(const KParams& P, const StepArgs& a, cudaStream_t st) {
+    primal_kernel<L, NS, MRT, S><<<blocks(P), kBlock, 0, st>>>(
+        P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags, a.obj);
+    return cudaGetLastError();
+  }
+  static cudaError_t objective(const KParams& P, const StepArgs& a, cudaStream_t st) {
+    objective_kernel<L, NS, MRT, S><<<blocks(P), kBlock, 0, st>>>(P, (const S*)a.Bin, a.theta,
+                                                                  a.flags, a.obj);
+    return cudaGetLastError();
+  }
+  static cudaError_t adjoint(const KParams& P, const StepArgs& a, cudaStream_t st) {
+    adjoint_kernel<L, NS, MRT, S><<<blocks(P), kBlock, 0, st>>>(
+        P, a.lam_in, (const S*)a.Bin, a.lam_out, a.theta, a.flags, a.grad, a.ws, a.stat_n,
+        a.has_next);
+    return cudaGetLastError();
+  }
+  static cudaError_t exportf(const KParams& P, const StepArgs& a, cudaStream_t st) {
+    export_kernel<L, NS, S><<<blocks(P), kBlock, 0, st>>>(P, (const S*)a.Bin, a.fout, a.post);
+    return cudaGetLastError();
+  }
+  static cudaError_t importf(const KParams& P, const StepArgs& a, cudaStream_t st) {
+    import_kernel<L, NS, S><<<blocks(P), kBlock, 0, st>>>(P, a.fin, (S*)a.Bout);
+    return cudaGetLastError();
+  }
+  static cudaError_t nonfinite(const KParams& P, const StepArgs& a, int M, cudaStream_t st) {
+    nonfinite_kernel<S><<<152 * 8, kBlock, 0, st>>>((const S*)a.Bin, (long long)M * P.N, a.count);
+    return cudaGetLastError();
+  }
+  static KernelSet set() {
+    return KernelSet{&primal, &objective, &adjoint, &exportf, &importf, &nonfinite, (int)sizeof(S)};
+  }
+};
+
+// Lookup of the instantiated set; defined in the per-lattice translation units.
+bool kernels_d2q9(int collision, int nscalars, int precision, KernelSet* out);
+bool kernels_d3q19_bgk(int nscalars, int precision, KernelSet* out);
+bool kernels_d3q19_mrt(int nscalars, int precision, KernelSet* out);
+
+}  // namespace albm

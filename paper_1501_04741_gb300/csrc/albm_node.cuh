@@ -1,0 +1,626 @@
+// Node operator W^x (Eq. "normal:iteration") and its transpose (Eq.
+// "adjoint:operator") for every node type, as device functions.
+//
+// Fluid populations are carried as deviations d_i = f_i - w_i from the rest
+// state (rho = 1, u = 0); this keeps the non-equilibrium part f - f_eq, a
+// small difference of O(1) numbers, accurate in FP32 and lets BF16/FP16
+// storage hold only the small part.  Scalars have a zero rest state and are
+// carried as they are.
+//
+// Interior collision (Sec. 3.1 and 3.2), per node with rho = 1 + drho,
+// u = j / rho and the post-collision velocity v = G(theta) u + g:
+//   deq_i(rho, u) = w_i (drho + rho P_i(u)),  P_i(u) = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u
+//   BGK  (Eq. SRT + Exact-Difference term):  W_i - w_i = deq_i(rho,v) + (1-omega)(d_i - deq_i(rho,u))
+//   FMRT (Sec. 3.1):                          W_i - w_i = deq_i(rho,v) + [U^-1 (I-T) U (d - deq(rho,u))]_i
+// with U^-1 (I-T) U = sum_k r_k U_k U_k^T, r_k = (1 - s_k) / |U_k|^2 (U has
+// orthogonal rows), a symmetric operator, so its transpose is itself.
+//
+// Reverse mode.  For adjoint weights a on the fluid outputs let
+//   H_a(rho, u) = sum_i a_i deq_i(rho, u) = drho A0 + rho (3 A1.u + 4.5 u.A2.u - 1.5 A0 u.u)
+// with A0 = sum a_i w_i, A1 = sum a_i w_i e_i, A2 = sum a_i w_i e_i e_i^T.  Then
+//   sum_i a_i W_i = H_a(rho, v) + sum_i c_i d_i - H_c(rho, u),  c = (1-omega) a  or  (U^-1(I-T)U) a,
+// whose partial derivatives give the adjoint of every population in a few
+// dot products (the paper reverse-differentiates W with TAPENADE, Sec. 3.4;
+// here the derivative is written out by hand and checked against the oracle).
+#pragma once
+#include <stdint.h>
+
+#include "albm_lattice.cuh"
+
+namespace albm {
+
+enum : uint8_t { FLUID = 0, WALL = 1, INLET = 2, OUTLET = 3, HOT = 4 };
+enum { OBJ_NONE = 0, OBJ_DISSIPATION = 1, OBJ_VARIANCE = 2, OBJ_HEATFLUX_DP = 3, OBJ_MIXFLUX = 4 };
+enum { POR_LINEAR = 0, POR_POWER = 1, POR_RAMP = 2 };
+
+// Constants of one problem, passed by value to every kernel.
+struct KParams {
+  int nx, ny, nz, nscal;
+  long long N;
+  float omega, one_m_omega, nu;
+  float gx, gy, gz;
+  float u_in, inv_1m_uin, rho_out, drho_out, one_m_rho_out;
+  float alpha_f, alpha_s;
+  int porosity;
+  float por_q;
+  int scalar_inlet;
+  float T_hot;
+  int objective;
+  float inv_A_in, inv_A_out;
+  float mrt_r[19];
+};
+
+// ---------------------------------------------------------------------------
+// porosity G(theta) (Sec. 3.2, theta = 1 - w) and diffusivity interpolation
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void porosity_G(const KParams& P, float th, float& G, float& dG) {
+  if (P.porosity == POR_LINEAR) {
+    G = 1.0f - th;
+    dG = -1.0f;
+  } else if (P.porosity == POR_POWER) {
+    const float q = P.por_q;
+    const float tq1 = th > 0.0f ? __powf(th, q - 1.0f) : (q == 1.0f ? 1.0f : 0.0f);
+    G = 1.0f - tq1 * th;
+    dG = -q * tq1;
+  } else {
+    const float den = 1.0f / (1.0f + P.por_q * th);
+    G = (1.0f - th) * den;
+    dG = -(1.0f + P.por_q) * den * den;
+  }
+}
+
+template <class LS>
+__device__ __forceinline__ void scalar_rate(const KParams& P, float th, float& om, float& dom) {
+  const float alpha = (1.0f - th) * P.alpha_f + th * P.alpha_s;
+  om = 1.0f / (0.5f + alpha * (1.0f / LS::cs2));
+  dom = -om * om * (P.alpha_s - P.alpha_f) * (1.0f / LS::cs2);
+}
+
+// ---------------------------------------------------------------------------
+// Node kernels for fluid lattice L with NS scalar lattices
+// ---------------------------------------------------------------------------
+template <class L, int NS, bool MRT>
+struct NodeOps {
+  using LS = typename ScalarOf<L>::type;
+  static constexpr int Q = L::Q;
+  static constexpr int QS = LS::Q;
+  static constexpr int M = Q + NS * QS;
+  static constexpr int NSA = NS > 0 ? NS : 1;
+
+  // y = U^-1 (I - T) U x  (symmetric; fully unrolled, constant U folded)
+  __device__ static __forceinline__ void mrt_op(const KParams& P, const float* x, float* y) {
+    float m[L::NMOM];
+#pragma unroll
+    for (int k = 0; k < L::NMOM; ++k) {
+      float s = 0.0f;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (L::U(k, i) != 0) s += float(L::U(k, i)) * x[i];
+      }
+      m[k] = s * P.mrt_r[k];
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      float s = 0.0f;
+#pragma unroll
+      for (int k = 0; k < L::NMOM; ++k) {
+        if (L::U(k, i) != 0) s += float(L::U(k, i)) * m[k];
+      }
+      y[i] = s;
+    }
+  }
+
+  // Zou-He (Sec. 3): reconstruct the unknown populations of an x face in
+  // place and return rho, drho, u.  Unknowns have e.n > 0 for the inward
+  // normal n; rho (1 - u.n) = s0 + 2 s_out from mass and normal momentum;
+  // each unknown is its opposite plus 2 w_i rho (e_i.u) / cs2, minus the
+  // transverse correction sum_t e_it N_t, N_t = 1/2 sum_{e.n = 0} f_k e_kt.
+  // In deviations the weights cancel: s0 + 2 s_out = 1 + D0 + 2 D_out.
+  __device__ static __forceinline__ void zou_he(const KParams& P, bool inlet, float* d, float& rho,
+                                                float& drho, float* u) {
+    float D0 = 0.0f, Dout = 0.0f, Ny = 0.0f, Nz = 0.0f;
+    const int sgn = inlet ? 1 : -1;  // inward normal along x
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int en = L::ex(i) * sgn;
+      if (en == 0) {
+        D0 += d[i];
+        if (L::ey(i)) Ny += float(L::ey(i)) * d[i];
+        if (L::ez(i)) Nz += float(L::ez(i)) * d[i];
+      } else if (en < 0) {
+        Dout += d[i];
+      }
+    }
+    Ny *= 0.5f;
+    Nz *= 0.5f;
+    if (inlet) {
+      drho = (D0 + 2.0f * Dout + P.u_in) * P.inv_1m_uin;
+      rho = 1.0f + drho;
+      u[0] = P.u_in;
+    } else {
+      rho = P.rho_out;
+      drho = P.drho_out;
+      u[0] = (D0 + 2.0f * Dout + P.one_m_rho_out) / P.rho_out;
+    }
+    u[1] = 0.0f;
+    u[2] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (L::ex(i) * sgn > 0) {
+        float v = d[L::opp(i)] + 6.0f * L::w(i) * rho * float(L::ex(i)) * u[0];
+        if (L::ey(i)) v -= float(L::ey(i)) * Ny;
+        if (L::ez(i)) v -= float(L::ez(i)) * Nz;
+        d[i] = v;
+      }
+    }
+  }
+
+  __device__ static __forceinline__ void moments(const float* d, float& rho, float& drho, float* u) {
+    float s = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      s += d[i];
+      if (L::ex(i)) jx += float(L::ex(i)) * d[i];
+      if (L::ey(i)) jy += float(L::ey(i)) * d[i];
+      if (L::ez(i)) jz += float(L::ez(i)) * d[i];
+    }
+    drho = s;
+    rho = 1.0f + s;
+    const float ir = 1.0f / rho;
+    u[0] = jx * ir;
+    u[1] = jy * ir;
+    u[2] = jz * ir;
+  }
+
+  __device__ static __forceinline__ float deq(int i, float rho, float drho, const float* u, float uu) {
+    const float eu = float(L::ex(i)) * u[0] + float(L::ey(i)) * u[1] + float(L::ez(i)) * u[2];
+    return L::w(i) * (drho + rho * (3.0f * eu + 4.5f * eu * eu - 1.5f * uu));
+  }
+
+  // Outlet scalar: unknowns (e_x < 0) at equilibrium with the node's own
+  // value T*, T* = sum_known g / (1 - sum_unknown w_i (1 + e_i.v / cs2)).
+  __device__ static __forceinline__ void scalar_outlet(float* g, const float* v, float& T, float& den) {
+    float sk = 0.0f, su = 0.0f;
+#pragma unroll
+    for (int i = 0; i < QS; ++i) {
+      if (LS::ex(i) >= 0) {
+        sk += g[i];
+      } else {
+        const float ev = float(LS::ex(i)) * v[0] + float(LS::ey(i)) * v[1] + float(LS::ez(i)) * v[2];
+        su += LS::w(i) * (1.0f + ev * (1.0f / LS::cs2));
+      }
+    }
+    den = 1.0f - su;
+    T = sk / den;
+#pragma unroll
+    for (int i = 0; i < QS; ++i) {
+      if (LS::ex(i) < 0) {
+        const float ev = float(LS::ex(i)) * v[0] + float(LS::ey(i)) * v[1] + float(LS::ez(i)) * v[2];
+        g[i] = LS::w(i) * T * (1.0f + ev * (1.0f / LS::cs2));
+      }
+    }
+  }
+
+  __device__ static __forceinline__ float inlet_value(const KParams& P, int s, int y) {
+    if (P.scalar_inlet == 1) {
+      const float c = (y >= P.ny / 2) ? 1.0f : 0.0f;
+      return (s & 1) ? 1.0f - c : c;
+    }
+    return 0.0f;
+  }
+
+  // -------------------------------------------------------------------------
+  // Forward: W^x applied to d (fluid deviations) and g (scalars) in place.
+  // obj1/obj2 receive this node's objective terms F^x(f^n(x)).
+  // -------------------------------------------------------------------------
+  __device__ static __forceinline__ void forward(const KParams& P, uint8_t type, float th, int y,
+                                                 float* d, float (*g)[QS], bool want_obj,
+                                                 double& obj1, double& obj2) {
+    if (type == WALL || type == HOT) {
+      float t[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) t[i] = d[L::opp(i)];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = t[i];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if (type == WALL) {
+          float tg[QS];
+#pragma unroll
+          for (int i = 0; i < QS; ++i) tg[i] = g[s][LS::opp(i)];
+#pragma unroll
+          for (int i = 0; i < QS; ++i) g[s][i] = tg[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < QS; ++i) g[s][i] = LS::w(i) * P.T_hot;
+        }
+      }
+      return;
+    }
+    float rho, drho, u[3];
+    if (type == INLET) {
+      zou_he(P, true, d, rho, drho, u);
+    } else if (type == OUTLET) {
+      zou_he(P, false, d, rho, drho, u);
+    } else {
+      moments(d, rho, drho, u);
+    }
+    if (want_obj && P.objective == OBJ_DISSIPATION && type == FLUID) {
+      obj1 += (double)dissipation(P, d, rho, drho, u);
+    }
+    float G, dG;
+    porosity_G(P, th, G, dG);
+    float v[3] = {G * u[0] + P.gx, G * u[1] + P.gy, G * u[2] + P.gz};
+    const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const float vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    if (MRT) {
+      float neq[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) neq[i] = d[i] - deq(i, rho, drho, u, uu);
+      float mn[Q];
+      mrt_op(P, neq, mn);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = deq(i, rho, drho, v, vv) + mn[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        d[i] = deq(i, rho, drho, v, vv) + P.one_m_omega * (d[i] - deq(i, rho, drho, u, uu));
+      }
+    }
+    if (NS == 0) return;
+    float om, dom;
+    scalar_rate<LS>(P, th, om, dom);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if (type == INLET) {
+        const float c = inlet_value(P, s, y);
+#pragma unroll
+        for (int i = 0; i < QS; ++i)
+          g[s][i] = LS::w(i) * c * (1.0f + float(LS::ex(i)) * P.u_in * (1.0f / LS::cs2));
+        continue;
+      }
+      float T, den;
+      if (type == OUTLET) {
+        scalar_outlet(g[s], v, T, den);
+        if (want_obj && s == 0) {
+          if (P.objective == OBJ_VARIANCE) {
+            obj1 += (double)T;
+            obj2 += (double)T * (double)T;
+          } else if (P.objective == OBJ_HEATFLUX_DP) {
+            obj1 += (double)v[0] * (double)T;
+          } else if (P.objective == OBJ_MIXFLUX) {
+            obj1 += (double)v[0] * (1.0 - (double)T * (double)T);
+          }
+        }
+      } else {
+        T = 0.0f;
+#pragma unroll
+        for (int i = 0; i < QS; ++i) T += g[s][i];
+      }
+#pragma unroll
+      for (int i = 0; i < QS; ++i) {
+        const float ev = float(LS::ex(i)) * v[0] + float(LS::ey(i)) * v[1] + float(LS::ez(i)) * v[2];
+        const float geq = LS::w(i) * T * (1.0f + ev * (1.0f / LS::cs2));
+        g[s][i] = g[s][i] + om * (geq - g[s][i]);
+      }
+    }
+    if (want_obj && type == INLET && P.objective == OBJ_HEATFLUX_DP) {
+      obj1 += -0.1 / 3.0 * (double)rho * (double)P.inv_A_in;
+    }
+  }
+
+  // Viscous dissipation 2 rho nu S:S of one node with
+  // S_ab = -(3 omega / (2 rho)) Pi_ab, Pi_ab = sum_i e_ia e_ib (f_i - feq_i)
+  //      = sum_i e_ia e_ib d_i - drho/3 delta_ab - j_a j_b / rho.
+  __device__ static __forceinline__ float dissipation(const KParams& P, const float* d, float rho,
+                                                      float drho, const float* u) {
+    float Pi[3][3];
+    pi_neq(d, rho, drho, u, Pi);
+    float s = 0.0f;
+#pragma unroll
+    for (int a = 0; a < L::DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < L::DIM; ++b) s += Pi[a][b] * Pi[a][b];
+    const float K = 9.0f * P.omega * P.omega * P.nu / rho;
+    return 0.5f * K * s;
+  }
+
+  __device__ static __forceinline__ void pi_neq(const float* d, float rho, float drho, const float* u,
+                                                float (*Pi)[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Pi[a][b] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
+#pragma unroll
+      for (int a = 0; a < L::DIM; ++a)
+#pragma unroll
+        for (int b = a; b < L::DIM; ++b)
+          if (e[a] * e[b] != 0) Pi[a][b] += float(e[a] * e[b]) * d[i];
+    }
+#pragma unroll
+    for (int a = 0; a < L::DIM; ++a) {
+#pragma unroll
+      for (int b = a; b < L::DIM; ++b) {
+        float v = Pi[a][b] - rho * u[a] * u[b];
+        if (a == b) v -= drho * (1.0f / 3.0f);
+        Pi[a][b] = v;
+        Pi[b][a] = v;
+      }
+    }
+  }
+
+  // -------------------------------------------------------------------------
+  // Reverse: given f^n(x) (d, g) and the adjoint weights a (fluid), b
+  // (scalars) of the node's outputs W^x, compute
+  //   lam_k  = sum_j a_j dW_j/dd_k + ws dF/dd_k,   lamg likewise,
+  //   dth    = sum_j a_j dW_j/dtheta + ws dF/dtheta.
+  // ws is the objective weight c_n of this step, cbar the outlet mean of
+  // scalar 0 at this step (variance objective).
+  // -------------------------------------------------------------------------
+  __device__ static __forceinline__ void reverse(const KParams& P, uint8_t type, float th, int y,
+                                                 const float* d_in, float (*g)[QS], const float* a,
+                                                 float (*b)[QS], float ws, float cbar, float* lam,
+                                                 float (*lamg)[QS], float& dth) {
+    dth = 0.0f;
+    if (type == WALL || type == HOT) {
+#pragma unroll
+      for (int k = 0; k < Q; ++k) lam[k] = a[L::opp(k)];
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int k = 0; k < QS; ++k) lamg[s][k] = (type == WALL) ? b[s][LS::opp(k)] : 0.0f;
+      return;
+    }
+    // ---- forward recomputation ----
+    float d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = d_in[i];
+    float rho, drho, u[3];
+    if (type == INLET) {
+      zou_he(P, true, d, rho, drho, u);
+    } else if (type == OUTLET) {
+      zou_he(P, false, d, rho, drho, u);
+    } else {
+      moments(d, rho, drho, u);
+    }
+    float G, dG;
+    porosity_G(P, th, G, dG);
+    const float v[3] = {G * u[0] + P.gx, G * u[1] + P.gy, G * u[2] + P.gz};
+    float dv[3] = {0.0f, 0.0f, 0.0f};
+    float ddrho = 0.0f;
+    float src[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) src[k] = 0.0f;
+    float dT0 = 0.0f;  // d(objective)/d(T of scalar 0)
+    float T[NSA], den[NSA];
+    float om = 1.0f, dom = 0.0f;
+    if (NS > 0) {
+      scalar_rate<LS>(P, th, om, dom);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        den[s] = 1.0f;
+        if (type == OUTLET) {
+          scalar_outlet(g[s], v, T[s], den[s]);
+        } else {
+          float t = 0.0f;
+#pragma unroll
+          for (int i = 0; i < QS; ++i) t += g[s][i];
+          T[s] = t;
+        }
+      }
+    }
+    // ---- objective sources ws * dF^x ----
+    if (ws != 0.0f) {
+      if (P.objective == OBJ_DISSIPATION && type == FLUID) {
+        float Pi[3][3];
+        pi_neq(d, rho, drho, u, Pi);
+        float s2 = 0.0f, tr = 0.0f;
+#pragma unroll
+        for (int a_ = 0; a_ < L::DIM; ++a_) {
+          tr += Pi[a_][a_];
+#pragma unroll
+          for (int b_ = 0; b_ < L::DIM; ++b_) s2 += Pi[a_][b_] * Pi[a_][b_];
+        }
+        const float ir = 1.0f / rho;
+        const float K = 9.0f * P.omega * P.omega * P.nu * ir;
+        const float Phi = 0.5f * K * s2;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+          const float e[3] = {float(L::ex(k)) - u[0], float(L::ey(k)) - u[1], float(L::ez(k)) - u[2]};
+          float q = 0.0f;
+#pragma unroll
+          for (int a_ = 0; a_ < L::DIM; ++a_)
+#pragma unroll
+            for (int b_ = 0; b_ < L::DIM; ++b_) q += e[a_] * Pi[a_][b_] * e[b_];
+          src[k] = ws * (K * (q - tr * (1.0f / 3.0f)) - Phi * ir);
+        }
+      } else if (NS > 0 && type == OUTLET) {
+        const float T0 = T[0];
+        if (P.objective == OBJ_VARIANCE) {
+          dT0 = ws * 2.0f * (T0 - cbar) * P.inv_A_out;
+        } else if (P.objective == OBJ_HEATFLUX_DP) {
+          dv[0] += ws * T0;
+          dT0 = ws * v[0];
+        } else if (P.objective == OBJ_MIXFLUX) {
+          dv[0] += ws * (1.0f - T0 * T0);
+          dT0 = ws * (-2.0f * v[0] * T0);
+        }
+      } else if (type == INLET && P.objective == OBJ_HEATFLUX_DP) {
+        ddrho += ws * (-0.1f / 3.0f) * P.inv_A_in;
+      }
+    }
+    // ---- scalar lattices ----
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if (type == INLET) {
+#pragma unroll
+        for (int k = 0; k < QS; ++k) lamg[s][k] = 0.0f;
+        continue;
+      }
+      float B0 = 0.0f, B1[3] = {0.0f, 0.0f, 0.0f}, bgsum = 0.0f;
+#pragma unroll
+      for (int i = 0; i < QS; ++i) {
+        const float bw = b[s][i] * LS::w(i);
+        B0 += bw;
+        if (LS::ex(i)) B1[0] += float(LS::ex(i)) * bw;
+        if (LS::ey(i)) B1[1] += float(LS::ey(i)) * bw;
+        if (LS::ez(i)) B1[2] += float(LS::ez(i)) * bw;
+        const float ev = float(LS::ex(i)) * v[0] + float(LS::ey(i)) * v[1] + float(LS::ez(i)) * v[2];
+        bgsum += b[s][i] * (LS::w(i) * T[s] * (1.0f + ev * (1.0f / LS::cs2)) - g[s][i]);
+      }
+      const float B1v = B1[0] * v[0] + B1[1] * v[1] + B1[2] * v[2];
+      float dTs = om * (B0 + B1v * (1.0f / LS::cs2)) + (s == 0 ? dT0 : 0.0f);
+      const float cT = om * T[s] * (1.0f / LS::cs2);
+      dv[0] += cT * B1[0];
+      dv[1] += cT * B1[1];
+      dv[2] += cT * B1[2];
+      dth += dom * bgsum;
+      if (type == OUTLET) {
+        // chain through g_i = w_i T* phi_i (unknowns) and T* = S_known / den
+        float dTstar = dTs;
+        float wex = 0.0f, wey = 0.0f, wez = 0.0f;  // sum over unknowns of w_i e_i
+#pragma unroll
+        for (int i = 0; i < QS; ++i) {
+          if (LS::ex(i) < 0) {
+            const float lg = (1.0f - om) * b[s][i];
+            const float ev = float(LS::ex(i)) * v[0] + float(LS::ey(i)) * v[1] + float(LS::ez(i)) * v[2];
+            dTstar += lg * LS::w(i) * (1.0f + ev * (1.0f / LS::cs2));
+            const float c = lg * LS::w(i) * T[s] * (1.0f / LS::cs2);
+            dv[0] += c * float(LS::ex(i));
+            dv[1] += c * float(LS::ey(i));
+            dv[2] += c * float(LS::ez(i));
+            wex += LS::w(i) * float(LS::ex(i));
+            wey += LS::w(i) * float(LS::ey(i));
+            wez += LS::w(i) * float(LS::ez(i));
+          }
+        }
+        const float iden = 1.0f / den[s];
+        const float cv = dTstar * T[s] * iden * (1.0f / LS::cs2);
+        dv[0] += cv * wex;
+        dv[1] += cv * wey;
+        dv[2] += cv * wez;
+#pragma unroll
+        for (int k = 0; k < QS; ++k)
+          lamg[s][k] = (LS::ex(k) >= 0) ? (1.0f - om) * b[s][k] + dTstar * iden : 0.0f;
+      } else {
+#pragma unroll
+        for (int k = 0; k < QS; ++k) lamg[s][k] = (1.0f - om) * b[s][k] + dTs;
+      }
+    }
+    // ---- fluid collision ----
+    float c[Q];
+    if (MRT) {
+      mrt_op(P, a, c);
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) c[i] = P.one_m_omega * a[i];
+    }
+    float A0 = 0.0f, A1[3] = {0.0f, 0.0f, 0.0f}, A2[3][3];
+    float C0 = 0.0f, C1[3] = {0.0f, 0.0f, 0.0f}, C2[3][3];
+#pragma unroll
+    for (int p_ = 0; p_ < 3; ++p_)
+#pragma unroll
+      for (int q_ = 0; q_ < 3; ++q_) {
+        A2[p_][q_] = 0.0f;
+        C2[p_][q_] = 0.0f;
+      }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
+      const float aw = a[i] * L::w(i);
+      const float cw = c[i] * L::w(i);
+      A0 += aw;
+      C0 += cw;
+#pragma unroll
+      for (int p_ = 0; p_ < 3; ++p_) {
+        if (e[p_]) {
+          A1[p_] += float(e[p_]) * aw;
+          C1[p_] += float(e[p_]) * cw;
+#pragma unroll
+          for (int q_ = p_; q_ < 3; ++q_) {
+            if (e[q_]) {
+              A2[p_][q_] += float(e[p_] * e[q_]) * aw;
+              C2[p_][q_] += float(e[p_] * e[q_]) * cw;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int p_ = 0; p_ < 3; ++p_)
+#pragma unroll
+      for (int q_ = 0; q_ < p_; ++q_) {
+        A2[p_][q_] = A2[q_][p_];
+        C2[p_][q_] = C2[q_][p_];
+      }
+    float A2v[3], C2u[3];
+#pragma unroll
+    for (int p_ = 0; p_ < 3; ++p_) {
+      A2v[p_] = A2[p_][0] * v[0] + A2[p_][1] * v[1] + A2[p_][2] * v[2];
+      C2u[p_] = C2[p_][0] * u[0] + C2[p_][1] * u[1] + C2[p_][2] * u[2];
+    }
+    const float vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const float Qa = 3.0f * (A1[0] * v[0] + A1[1] * v[1] + A1[2] * v[2]) +
+                     4.5f * (A2v[0] * v[0] + A2v[1] * v[1] + A2v[2] * v[2]) - 1.5f * A0 * vv;
+    const float Qc = 3.0f * (C1[0] * u[0] + C1[1] * u[1] + C1[2] * u[2]) +
+                     4.5f * (C2u[0] * u[0] + C2u[1] * u[1] + C2u[2] * u[2]) - 1.5f * C0 * uu;
+    ddrho += (A0 + Qa) - (C0 + Qc);
+    float du[3];
+#pragma unroll
+    for (int p_ = 0; p_ < 3; ++p_) {
+      dv[p_] += rho * (3.0f * A1[p_] + 9.0f * A2v[p_] - 3.0f * A0 * v[p_]);
+      du[p_] = G * dv[p_] - rho * (3.0f * C1[p_] + 9.0f * C2u[p_] - 3.0f * C0 * u[p_]);
+    }
+    dth += dG * (u[0] * dv[0] + u[1] * dv[1] + u[2] * dv[2]);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) lam[k] = c[k] + src[k];
+    if (type == FLUID) {
+      const float ir = 1.0f / rho;
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        const float eu = (float(L::ex(k)) - u[0]) * du[0] + (float(L::ey(k)) - u[1]) * du[1] +
+                         (float(L::ez(k)) - u[2]) * du[2];
+        lam[k] += ddrho + eu * ir;
+      }
+      return;
+    }
+    // ---- Zou-He transpose ----
+    const bool inlet = (type == INLET);
+    const int sgn = inlet ? 1 : -1;
+    // total sensitivity of the face scalar (rho at the inlet, u_x at the outlet)
+    float dface = inlet ? ddrho : du[0];
+    float dNy = 0.0f, dNz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (L::ex(i) * sgn > 0) {
+        const float coef = 6.0f * L::w(i) * float(L::ex(i));
+        dface += lam[i] * coef * (inlet ? u[0] : rho);
+        if (L::ey(i)) dNy -= lam[i] * float(L::ey(i));
+        if (L::ez(i)) dNz -= lam[i] * float(L::ez(i));
+      }
+    }
+    // d(face scalar)/d(D0) and /d(Dout): 1/(1-u_in), 2/(1-u_in) at the inlet;
+    // 1/rho_out, 2/rho_out at the outlet
+    const float k1 = inlet ? P.inv_1m_uin : 1.0f / P.rho_out;
+    float out[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const int en = L::ex(k) * sgn;
+      if (en > 0) {
+        out[k] = 0.0f;
+      } else if (en < 0) {
+        out[k] = lam[k] + lam[L::opp(k)] + 2.0f * k1 * dface;
+      } else {
+        out[k] = lam[k] + k1 * dface + 0.5f * (float(L::ey(k)) * dNy + float(L::ez(k)) * dNz);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < Q; ++k) lam[k] = out[k];
+  }
+};
+
+}  // namespace albm
