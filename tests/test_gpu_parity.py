@@ -6,7 +6,11 @@ Tolerances (FP32 kernels against FP64):
 * one adjoint step from the same state and lambda: <= 2e-5 of max|lambda|
   (and of max|dJ/dtheta| for the theta terms);
 * whole trajectories: populations within 1e-5 of max|f| after the stated
-  steps, J within 1e-5 relative, dJ/dtheta within 1e-4 (inf-norm relative).
+  steps and dJ/dtheta within 1e-4 (inf-norm relative), the two bars the
+  problem statement fixes; J within 1e-4 relative.  J has no stated bar:
+  the dissipation objective is quadratic in f - f_eq, about 1e-3 of |f| at
+  these flow speeds, so a population error of 1e-5 |f| allows a relative J
+  error of order 2e-5 |f| / |f - f_eq|; J is gated like the gradient.
 Lattice sizes are odd so that the node count leaves a ragged last block.
 """
 import numpy as np
@@ -136,7 +140,7 @@ def test_trajectory_objective_and_gradient(name):
         s.adjoint_step(P.nsteps)
         grad = _np(s.gradient())
     assert np.abs(f_gpu - fN).max() <= 1e-5 * np.abs(fN).max()
-    assert abs(J_gpu - J) <= 1e-5 * abs(J) + 1e-12
+    assert abs(J_gpu - J) <= 1e-4 * abs(J) + 1e-12
     assert np.abs(grad - g).max() <= 1e-4 * np.abs(g).max()
 
 
@@ -177,7 +181,7 @@ def test_channel2d_full_config_parity():
         s.adjoint_step(P.nsteps)
         grad = _np(s.gradient())
     assert np.abs(f_gpu - fN).max() <= 1e-5 * np.abs(fN).max()
-    assert abs(J_gpu - J) <= 1e-5 * abs(J)
+    assert abs(J_gpu - J) <= 1e-4 * abs(J)
     assert np.abs(grad - g).max() <= 1e-4 * np.abs(g).max()
     # and within 1e-3 of central differences of the FP64 objective
     for i in list(np.argsort(-np.abs(g))[:3]):
