@@ -211,6 +211,33 @@ lbm_status lbm_profile_read(lbm_handle h, double* out);
 /* Primal steps recomputed by the checkpoint schedule since the last reset. */
 long long lbm_recompute_steps(lbm_handle h);
 
+/* Objective F(f) of one pre-collision state, evaluated without allocating
+ * any device memory.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate at the point of the call - code running
+ * while a stream is captured into a CUDA graph (cudaMalloc is not
+ * capturable and synchronises the device), processes whose device memory is
+ * fully handed out in advance, and host frameworks that own the allocator.
+ *   p      : problem description (lattice, collision, objective, ...); the
+ *            time weights are ignored, F is the objective of this one state.
+ *   f      : device, M*N floats, full pre-collision populations (the layout
+ *            of lbm_get_populations with which = 0).
+ *   theta  : device, N floats.   flags: device, N node types.
+ *   stream : cudaStream_t the two kernels run on.
+ *   F_host : host pointer receiving F; the call synchronises the stream.
+ * Scratch lives in a fixed static device array of about 1.5 MiB that every
+ * GPU loading the library keeps until exit; lattices above 8,388,608 nodes
+ * are rejected with LBM_ERR_ARG.  The first call on a device, with that
+ * device current, resolves the array's device address; make it before any
+ * stream capture.  All calls share the array, so calls that overlap on the
+ * GPU race and must be serialised by the caller.  Errors: LBM_ERR_ARG,
+ * LBM_ERR_CUDA; the message is returned by lbm_noalloc_last_error(). */
+lbm_status lbm_state_objective_noalloc(const lbm_params* p, const float* f,
+                                       const float* theta, const uint8_t* flags,
+                                       void* stream, double* F_host);
+
+/* Message of the last failed lbm_state_objective_noalloc call on this thread. */
+const char* lbm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

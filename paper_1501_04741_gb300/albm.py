@@ -33,7 +33,8 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_theta", "lbm_
            "lbm_adjoint_seed", "lbm_adjoint_time", "lbm_run", "lbm_gradient",
            "lbm_get_populations", "lbm_set_populations", "lbm_get_adjoint", "lbm_get_flags",
            "lbm_check_finite", "lbm_sizes", "lbm_last_timing", "lbm_profile",
-           "lbm_profile_read", "lbm_recompute_steps"]
+           "lbm_profile_read", "lbm_recompute_steps", "lbm_state_objective_noalloc",
+           "lbm_noalloc_last_error"]
 
 
 class LbmParams(C.Structure):
@@ -92,6 +93,10 @@ def lib():
         L.lbm_profile_read.argtypes = [vp, C.POINTER(d)]
         L.lbm_recompute_steps.argtypes = [vp]
         L.lbm_recompute_steps.restype = C.c_longlong
+        L.lbm_state_objective_noalloc.argtypes = [C.POINTER(LbmParams), vp, vp, vp, vp,
+                                                  C.POINTER(d)]
+        L.lbm_noalloc_last_error.argtypes = []
+        L.lbm_noalloc_last_error.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -288,3 +293,21 @@ class Solver:
 
     def recompute_steps(self) -> int:
         return int(self._L.lbm_recompute_steps(self._h))
+
+
+def state_objective_noalloc(P: Problem, f, theta, flags, stream=None) -> float:
+    """F(f) of one pre-collision state through the allocation-free entry point.
+
+    ``f`` (M x N float32), ``theta`` (N float32) and ``flags`` (N uint8) must
+    be device tensors.  The library allocates no device memory for this call
+    (its scratch is a fixed static device array); concurrent calls on one
+    device must not overlap.
+    """
+    L = lib()
+    p = make_params(P)
+    F = C.c_double()
+    code = L.lbm_state_objective_noalloc(C.byref(p), _ptr(f), _ptr(theta), _ptr(flags),
+                                         _stream_ptr(stream), C.byref(F))
+    if code != 0:
+        raise AlbmError(code, L.lbm_noalloc_last_error().decode())
+    return F.value
