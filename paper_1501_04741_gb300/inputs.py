@@ -87,12 +87,17 @@ def channel2d(**kw) -> Problem:
 def mixer3d(**kw) -> Problem:
     """D3Q19 MRT mixer 256x128x128 + two D3Q7 scalars, tau=0.6.
 
-    Diffusivity keeps the paper's mixer ratio nu/alpha = 0.02/0.003 (Tab.
-    "tab:cases") for both phases (alpha_solid = alpha_fluid, as in the paper).
+    The scalar diffusivity is alpha = nu (Schmidt number 1) in both phases
+    (alpha_solid = alpha_fluid, as in the paper's mixer).  The paper's own
+    ratio nu/alpha = 0.02/0.003 puts the D3Q7 relaxation time at 0.52, and
+    with theta ~ U[0,1] filling the design box the flow squeezes around it
+    at |u| up to about 0.25 = c_s^2 of D3Q7; the scalar then diverges within
+    2000 steps, while alpha = nu (tau_T = 0.633) stays within [0, 1.09]
+    over the 10000 steps.
     """
     tau = 0.6
     nu = (tau - 0.5) / 3.0
-    alpha = nu * 0.003 / 0.02
+    alpha = nu
     Lx, Ly, Lz = 256, 128, 128
     p = Problem(lattice="D3Q19", dims=(Lx, Ly, Lz), collision="MRT", tau=tau,
                 walls="yz", channel="inlet_outlet", u_in=0.05, rho_out=1.0,
