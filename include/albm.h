@@ -177,6 +177,11 @@ lbm_status lbm_gradient(lbm_handle h, double* dst);
  *   which = 1: post-collision W(f^{n-1}(x)) at x, before streaming. */
 lbm_status lbm_get_populations(lbm_handle h, float* dst, int which);
 
+/* As lbm_get_populations for the state of an earlier time that the handle
+ * still holds (a checkpoint, or the state the adjoint last used);
+ * LBM_ERR_STATE when that state is not held. */
+lbm_status lbm_get_populations_at(lbm_handle h, int time, float* dst, int which);
+
 /* Overwrite the current state with pre-collision populations src (M*N
  * floats, host or device, full values); drops stored states. */
 lbm_status lbm_set_populations(lbm_handle h, const float* src);

@@ -31,7 +31,7 @@ STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_theta", "lbm_reset",
            "lbm_primal_step", "lbm_time", "lbm_objective", "lbm_adjoint_step",
            "lbm_adjoint_seed", "lbm_adjoint_time", "lbm_run", "lbm_gradient",
-           "lbm_get_populations", "lbm_set_populations", "lbm_get_adjoint", "lbm_get_flags",
+           "lbm_get_populations", "lbm_get_populations_at", "lbm_set_populations", "lbm_get_adjoint", "lbm_get_flags",
            "lbm_check_finite", "lbm_sizes", "lbm_last_timing", "lbm_profile",
            "lbm_profile_read", "lbm_recompute_steps", "lbm_state_objective_noalloc",
            "lbm_noalloc_last_error"]
@@ -85,6 +85,7 @@ def lib():
         L.lbm_objective.argtypes = [vp, C.POINTER(d)]
         L.lbm_gradient.argtypes = [vp, vp]
         L.lbm_get_populations.argtypes = [vp, vp, i]
+        L.lbm_get_populations_at.argtypes = [vp, i, vp, i]
         L.lbm_get_adjoint.argtypes = [vp, vp]
         L.lbm_get_flags.argtypes = [vp, vp]
         L.lbm_check_finite.argtypes = [vp, C.POINTER(C.c_longlong)]
@@ -252,6 +253,14 @@ class Solver:
         if out is None:
             out = torch.empty((self.M, self.N), dtype=torch.float32, device="cuda")
         self._check(self._L.lbm_get_populations(self._h, _ptr(out), int(which)))
+        return out
+
+    def populations_at(self, time: int, which: int = 0, out=None):
+        """Populations of an earlier time the handle still holds."""
+        import torch
+        if out is None:
+            out = torch.empty((self.M, self.N), dtype=torch.float32, device="cuda")
+        self._check(self._L.lbm_get_populations_at(self._h, int(time), _ptr(out), int(which)))
         return out
 
     def set_populations(self, f):

@@ -670,10 +670,9 @@ lbm_status lbm_gradient(lbm_handle h, double* dst) {
   return LBM_OK;
 }
 
-lbm_status lbm_get_populations(lbm_handle h, float* dst, int which) {
-  if (!h || !dst) return LBM_ERR_ARG;
-  const int b = find_buf(h, h->t);
-  if (b < 0) FAIL(h, LBM_ERR_STATE, "current state not held");
+static lbm_status export_state(lbm_handle h, int time, float* dst, int which) {
+  const int b = find_buf(h, time);
+  if (b < 0) FAIL(h, LBM_ERR_STATE, "state of time %d is not held", time);
   const bool dev = is_device_ptr(dst);
   float* out = dst;
   if (!dev) CK(h, cudaMalloc(&out, sizeof(float) * (size_t)h->M * (size_t)h->N));
@@ -691,6 +690,16 @@ lbm_status lbm_get_populations(lbm_handle h, float* dst, int which) {
   }
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "export: %s", cudaGetErrorString(e));
   return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_handle h, float* dst, int which) {
+  if (!h || !dst) return LBM_ERR_ARG;
+  return export_state(h, h->t, dst, which);
+}
+
+lbm_status lbm_get_populations_at(lbm_handle h, int time, float* dst, int which) {
+  if (!h || !dst) return LBM_ERR_ARG;
+  return export_state(h, time, dst, which);
 }
 
 lbm_status lbm_set_populations(lbm_handle h, const float* src) {

@@ -23,11 +23,30 @@
 
 namespace albm {
 
+// ---- launch tunables (minimum resident blocks per SM of 256 threads) -----
+#ifndef ALBM_PRIMAL_MINB
+#define ALBM_PRIMAL_MINB 1
+#endif
+#ifndef ALBM_ADJOINT_MINB
+#define ALBM_ADJOINT_MINB 1
+#endif
+// streaming (evict-first) stores for the state and adjoint outputs, which
+// the same kernel never reads back
+#ifndef ALBM_STREAM_STORES
+#define ALBM_STREAM_STORES 0
+#endif
+
 // ---- storage conversions -------------------------------------------------
 __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
-__device__ __forceinline__ void st(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st(float* p, float v) {
+#if ALBM_STREAM_STORES
+  __stcs(p, v);
+#else
+  *p = v;
+#endif
+}
 __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 
@@ -119,7 +138,7 @@ struct Gather {
 // primal step: B^{n+1}(x) = W^x(f^n(x)); optional objective terms of f^n
 // ---------------------------------------------------------------------------
 template <class L, int NS, bool MRT, class S>
-__global__ void __launch_bounds__(256) primal_kernel(KParams P, const S* __restrict__ Bin,
+__global__ void __launch_bounds__(256, ALBM_PRIMAL_MINB) primal_kernel(KParams P, const S* __restrict__ Bin,
                                                      S* __restrict__ Bout,
                                                      const float* __restrict__ theta,
                                                      const uint8_t* __restrict__ flags,
@@ -173,7 +192,7 @@ __global__ void __launch_bounds__(256) objective_kernel(KParams P, const S* __re
 // adjoint step: lambda^n(x) from lambda^{n+1}(x + e_j) and f^n(x)
 // ---------------------------------------------------------------------------
 template <class L, int NS, bool MRT, class S>
-__global__ void __launch_bounds__(256) adjoint_kernel(KParams P, const float* __restrict__ lam_in,
+__global__ void __launch_bounds__(256, ALBM_ADJOINT_MINB) adjoint_kernel(KParams P, const float* __restrict__ lam_in,
                                                       const S* __restrict__ Bn,
                                                       float* __restrict__ lam_out,
                                                       const float* __restrict__ theta,
@@ -213,11 +232,11 @@ __global__ void __launch_bounds__(256) adjoint_kernel(KParams P, const float* __
   float lam[Q], lamg[NSA][QS], dth;
   Ops::reverse(P, type, theta[idx], geo.y, d, g, a, b, ws, cbar, lam, lamg, dth);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) lam_out[(long long)i * P.N + idx] = lam[i];
+  for (int i = 0; i < Q; ++i) st(lam_out + (long long)i * P.N + idx, lam[i]);
 #pragma unroll
   for (int s = 0; s < NS; ++s)
 #pragma unroll
-    for (int i = 0; i < QS; ++i) lam_out[(long long)(Q + s * QS + i) * P.N + idx] = lamg[s][i];
+    for (int i = 0; i < QS; ++i) st(lam_out + (long long)(Q + s * QS + i) * P.N + idx, lamg[s][i]);
   if (type == FLUID || type == INLET || type == OUTLET) grad[idx] += (double)dth;
 }
 
