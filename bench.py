@@ -268,7 +268,7 @@ def run_ours(args):
         dt = time.perf_counter() - t0
         e2e = {"value": world * updates_per_step * max(1, args.e2e_steps) / dt / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(N * 4), "d2h_bytes_per_step": int(N * 8 + 16 * (P.nsteps + 1))}
-    launches = args.steps * (P.nsteps + 1 + P.nsteps + 1) + recompute
+    launches = prof["launches"]
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, cores, sample = oracle_sample(P)

@@ -210,7 +210,8 @@ lbm_status lbm_profile(lbm_handle h, int enable);
 
 /* Read and clear the kernel timing record (synchronises): out[8] =
  * {primal launches, primal ms, recompute launches, recompute ms,
- *  adjoint launches, adjoint ms, 0, 0}. */
+ *  adjoint launches, adjoint ms, other launches (objective and record
+ *  folding), total launches}. */
 lbm_status lbm_profile_read(lbm_handle h, double* out);
 
 /* Primal steps recomputed by the checkpoint schedule since the last reset. */

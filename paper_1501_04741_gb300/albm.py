@@ -298,7 +298,8 @@ class Solver:
         self._check(self._L.lbm_profile_read(self._h, out))
         v = list(out)
         return {"primal": (int(v[0]), v[1]), "recompute": (int(v[2]), v[3]),
-                "adjoint": (int(v[4]), v[5])}
+                "adjoint": (int(v[4]), v[5]), "other_launches": int(v[6]),
+                "launches": int(v[7])}
 
     def recompute_steps(self) -> int:
         return int(self._L.lbm_recompute_steps(self._h))

@@ -44,7 +44,8 @@ struct lbm_ctx {
   uint8_t* flags = nullptr;
   float* theta = nullptr;
   double* grad = nullptr;
-  double* stats = nullptr;          // 2 doubles per step 0..nsteps
+  double* stats = nullptr;          // 2 doubles per step 0..nsteps (folded)
+  double* stats_raw = nullptr;      // kObjSlots pairs per step (accumulated)
   unsigned long long* counter = nullptr;
   float* lam[2] = {nullptr, nullptr};
   int lam_cur = 0;
@@ -67,6 +68,7 @@ struct lbm_ctx {
   float last_primal_ms = 0.f, last_adjoint_ms = 0.f;
   bool primal_timed = false, adjoint_timed = false;
   long long recompute_steps = 0;
+  long long launches_other = 0;     // objective / fold / import / export kernels
   std::string err;
 };
 
@@ -213,7 +215,9 @@ static lbm_status launch_primal(lbm_ctx* h, int src, int dst, int t, bool record
   StepArgs a = blank_args(h);
   a.Bin = h->bufs[src];
   a.Bout = h->bufs[dst];
-  a.obj = (record && t <= h->p.nsteps && h->c[t] != 0.0) ? h->stats + 2 * (size_t)t : nullptr;
+  a.obj = (record && t <= h->p.nsteps && h->c[t] != 0.0)
+              ? h->stats_raw + 2 * (size_t)albm::kObjSlots * (size_t)t
+              : nullptr;
   int slot;
   prof_begin(h, kind, &slot);
   cudaError_t e = h->ks.primal(h->kp, a, h->stream);
@@ -227,8 +231,9 @@ static lbm_status record_final_objective(lbm_ctx* h) {
   if (t > h->p.nsteps || h->c[t] == 0.0 || h->p.objective == LBM_OBJ_NONE) return LBM_OK;
   StepArgs a = blank_args(h);
   a.Bin = h->bufs[find_buf(h, t)];
-  a.obj = h->stats + 2 * (size_t)t;
+  a.obj = h->stats_raw + 2 * (size_t)albm::kObjSlots * (size_t)t;
   cudaError_t e = h->ks.objective(h->kp, a, h->stream);
+  h->launches_other++;
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "objective kernel launch: %s", cudaGetErrorString(e));
   return LBM_OK;
 }
@@ -323,6 +328,32 @@ static lbm_status do_reset(lbm_ctx* h) {
   h->t_adj = -1;
   h->recompute_steps = 0;
   CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * 2 * (size_t)(h->p.nsteps + 1), h->stream));
+  CK(h, cudaMemsetAsync(h->stats_raw, 0,
+                        sizeof(double) * 2 * albm::kObjSlots * (size_t)(h->p.nsteps + 1), h->stream));
+  return LBM_OK;
+}
+
+namespace albm {
+// stats[n][k] = sum over slots of raw[n][slot][k], n in [n0, n1]
+__global__ void fold_stats_kernel(const double* __restrict__ raw, double* __restrict__ stats,
+                                  int n0, int n1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = n0 + i / 2, k = i % 2;
+  if (n > n1) return;
+  double acc = 0.0;
+  for (int s = 0; s < kObjSlots; ++s) acc += raw[((long long)n * kObjSlots + s) * 2 + k];
+  stats[2 * (long long)n + k] = acc;
+}
+}  // namespace albm
+
+// fold the slot accumulators of steps n0..n1 into the per-step record
+static lbm_status fold_stats(lbm_ctx* h, int n0, int n1) {
+  if (n1 < n0 || h->p.objective == LBM_OBJ_NONE) return LBM_OK;
+  const int threads = 2 * (n1 - n0 + 1);
+  albm::fold_stats_kernel<<<(threads + 255) / 256, 256, 0, h->stream>>>(h->stats_raw, h->stats,
+                                                                          n0, n1);
+  h->launches_other++;
+  CK(h, cudaGetLastError());
   return LBM_OK;
 }
 
@@ -443,6 +474,7 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   CKC(cudaMalloc(&h->theta, sizeof(float) * (size_t)h->N));
   CKC(cudaMalloc(&h->grad, sizeof(double) * (size_t)h->N));
   CKC(cudaMalloc(&h->stats, sizeof(double) * 2 * (size_t)(p.nsteps + 1)));
+  CKC(cudaMalloc(&h->stats_raw, sizeof(double) * 2 * albm::kObjSlots * (size_t)(p.nsteps + 1)));
   CKC(cudaMalloc(&h->counter, sizeof(unsigned long long)));
   CKC(cudaMalloc(&h->lam[0], sizeof(float) * (size_t)h->M * (size_t)h->N));
   CKC(cudaMalloc(&h->lam[1], sizeof(float) * (size_t)h->M * (size_t)h->N));
@@ -473,7 +505,7 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   if (budget <= 0) {
     size_t fr = 0, tot = 0;
     CKC(cudaMemGetInfo(&fr, &tot));
-    budget = 0.6 * (double)fr;
+    budget = 0.8 * (double)fr;
   }
   h->max_bufs = (int)std::max(3.0, std::floor(budget / (double)h->state_bytes));
   // level-1 checkpoint stride: given, or every state if all fit, else
@@ -500,6 +532,7 @@ void lbm_destroy(lbm_handle h) {
   cudaFree(h->theta);
   cudaFree(h->grad);
   cudaFree(h->stats);
+  cudaFree(h->stats_raw);
   cudaFree(h->counter);
   cudaFree(h->lam[0]);
   cudaFree(h->lam[1]);
@@ -533,6 +566,7 @@ lbm_status lbm_primal_step(lbm_handle h, int k) {
          h->p.nsteps);
   if (h->t_adj >= 0) FAIL(h, LBM_ERR_STATE, "the adjoint of this trajectory has started; reset first");
   CK(h, cudaEventRecord(h->t0, h->stream));
+  const int t_begin = h->t;
   for (int i = 0; i < k; ++i) {
     const int src = find_buf(h, h->t);
     int dst;
@@ -546,6 +580,10 @@ lbm_status lbm_primal_step(lbm_handle h, int k) {
   }
   if (k > 0 && h->t == h->p.nsteps) {
     lbm_status s = record_final_objective(h);
+    if (s) return s;
+  }
+  if (k > 0) {
+    lbm_status s = fold_stats(h, t_begin, h->t);
     if (s) return s;
   }
   CK(h, cudaEventRecord(h->t1, h->stream));
@@ -631,6 +669,7 @@ lbm_status lbm_profile(lbm_handle h, int enable) {
   if (!h) return LBM_ERR_ARG;
   CK(h, cudaStreamSynchronize(h->stream));
   h->profile = enable != 0;
+  h->launches_other = 0;
   h->ev_used.clear();
   h->ev_next = 0;
   return LBM_OK;
@@ -646,6 +685,9 @@ lbm_status lbm_profile_read(lbm_handle h, double* out) {
     out[2 * u.first] += 1.0;
     out[2 * u.first + 1] += ms;
   }
+  out[6] = (double)h->launches_other;
+  out[7] = out[0] + out[2] + out[4] + out[6];
+  h->launches_other = 0;
   h->ev_used.clear();
   h->ev_next = 0;
   return LBM_OK;
@@ -730,6 +772,8 @@ lbm_status lbm_set_populations(lbm_handle h, const float* src) {
   h->t = 0;
   h->t_adj = -1;
   CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * 2 * (size_t)(h->p.nsteps + 1), h->stream));
+  CK(h, cudaMemsetAsync(h->stats_raw, 0,
+                        sizeof(double) * 2 * albm::kObjSlots * (size_t)(h->p.nsteps + 1), h->stream));
   return LBM_OK;
 }
 

@@ -25,7 +25,7 @@ namespace albm {
 
 // ---- launch tunables (minimum resident blocks per SM of 256 threads) -----
 #ifndef ALBM_PRIMAL_MINB
-#define ALBM_PRIMAL_MINB 1
+#define ALBM_PRIMAL_MINB 4
 #endif
 #ifndef ALBM_ADJOINT_MINB
 #define ALBM_ADJOINT_MINB 1
@@ -83,6 +83,11 @@ __device__ __forceinline__ Geo make_geo(const KParams& P, long long idx) {
   g.ozp = ((g.z == P.nz - 1) ? -(P.nz - 1) : 1) * sxy;
   return g;
 }
+
+// Per-step objective sums are spread over kObjSlots accumulator pairs (block
+// index modulo kObjSlots) so that the blocks of one launch do not all
+// serialise on one address; fold_stats_kernel adds the slots afterwards.
+constexpr int kObjSlots = 64;
 
 // ---- block reduction of two doubles into global accumulators -------------
 __device__ __forceinline__ void block_sum2(double a, double b, double* out) {
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(256, ALBM_PRIMAL_MINB) primal_kernel(KParams P
 #pragma unroll
       for (int i = 0; i < QS; ++i) st(Bout + (long long)(Q + s * QS + i) * P.N + idx, g[s][i]);
   }
-  if (obj != nullptr) block_sum2(o1, o2, obj);
+  if (obj != nullptr) block_sum2(o1, o2, obj + 2 * (blockIdx.x % kObjSlots));
 }
 
 // objective terms of f^n only (no state write), used for F(f^N)
@@ -185,8 +190,9 @@ __global__ void __launch_bounds__(256) objective_kernel(KParams P, const S* __re
       Ops::forward(P, type, theta[idx], geo.y, d, g, true, o1, o2);
     }
   }
-  block_sum2(o1, o2, obj);
+  block_sum2(o1, o2, obj + 2 * (blockIdx.x % kObjSlots));
 }
+
 
 // ---------------------------------------------------------------------------
 // adjoint step: lambda^n(x) from lambda^{n+1}(x + e_j) and f^n(x)
@@ -206,31 +212,34 @@ __global__ void __launch_bounds__(256, ALBM_ADJOINT_MINB) adjoint_kernel(KParams
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= P.N) return;
   const Geo geo = make_geo(P, idx);
-  float d[Q], g[NSA][QS], a[Q], b[NSA][QS];
+  float d[Q], g[NSA][QS];
   Gather<L, NS, S>::pre(geo, P.N, Bn, d, g);
-  if (has_next) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-      a[i] = __ldg(lam_in + (long long)i * P.N + idx + geo.off(L::ex(i), L::ey(i), L::ez(i)));
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-#pragma unroll
-      for (int i = 0; i < QS; ++i)
-        b[s][i] = __ldg(lam_in + (long long)(Q + s * QS + i) * P.N + idx +
-                        geo.off(LS::ex(i), LS::ey(i), LS::ez(i)));
-  } else {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) a[i] = 0.0f;
-#pragma unroll
-    for (int s = 0; s < NSA; ++s)
-#pragma unroll
-      for (int i = 0; i < QS; ++i) b[s][i] = 0.0f;
-  }
   const uint8_t type = flags[idx];
   // outlet mean of scalar 0 at this step (variance objective)
   const float cbar = stat_n != nullptr ? (float)(stat_n[0] * (double)P.inv_A_out) : 0.0f;
+  // lambda^{n+1}_j(x + e_j), or zero for the first (source-only) step
+  auto load = [&](float* a, float (*b)[QS]) {
+    if (has_next) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        a[i] = __ldg(lam_in + (long long)i * P.N + idx + geo.off(L::ex(i), L::ey(i), L::ez(i)));
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int i = 0; i < QS; ++i)
+          b[s][i] = __ldg(lam_in + (long long)(Q + s * QS + i) * P.N + idx +
+                          geo.off(LS::ex(i), LS::ey(i), LS::ez(i)));
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) a[i] = 0.0f;
+#pragma unroll
+      for (int s = 0; s < NSA; ++s)
+#pragma unroll
+        for (int i = 0; i < QS; ++i) b[s][i] = 0.0f;
+    }
+  };
   float lam[Q], lamg[NSA][QS], dth;
-  Ops::reverse(P, type, theta[idx], geo.y, d, g, a, b, ws, cbar, lam, lamg, dth);
+  Ops::reverse(P, type, theta[idx], geo.y, d, g, load, ws, cbar, lam, lamg, dth);
 #pragma unroll
   for (int i = 0; i < Q; ++i) st(lam_out + (long long)i * P.N + idx, lam[i]);
 #pragma unroll

@@ -33,6 +33,10 @@ enum : uint8_t { FLUID = 0, WALL = 1, INLET = 2, OUTLET = 3, HOT = 4 };
 enum { OBJ_NONE = 0, OBJ_DISSIPATION = 1, OBJ_VARIANCE = 2, OBJ_HEATFLUX_DP = 3, OBJ_MIXFLUX = 4 };
 enum { POR_LINEAR = 0, POR_POWER = 1, POR_RAMP = 2 };
 
+#ifndef ALBM_ADJ_TWO_PHASE
+#define ALBM_ADJ_TWO_PHASE 1
+#endif
+
 // Constants of one problem, passed by value to every kernel.
 struct KParams {
   int nx, ny, nz, nscal;
@@ -360,12 +364,18 @@ struct NodeOps {
   // ws is the objective weight c_n of this step, cbar the outlet mean of
   // scalar 0 at this step (variance objective).
   // -------------------------------------------------------------------------
+  // The adjoint weights are fetched by load(a, b) only after the forward
+  // quantities are recomputed (two phases: f^n first, lambda^{n+1} second),
+  // which bounds the number of values live in registers at once.
+  template <class Loader>
   __device__ static __forceinline__ void reverse(const KParams& P, uint8_t type, float th, int y,
-                                                 const float* d_in, float (*g)[QS], const float* a,
-                                                 float (*b)[QS], float ws, float cbar, float* lam,
-                                                 float (*lamg)[QS], float& dth) {
+                                                 const float* d_in, float (*g)[QS],
+                                                 const Loader& load, float ws, float cbar,
+                                                 float* lam, float (*lamg)[QS], float& dth) {
     dth = 0.0f;
+    float a[Q], b[NSA][QS];
     if (type == WALL || type == HOT) {
+      load(a, b);
 #pragma unroll
       for (int k = 0; k < Q; ++k) lam[k] = a[L::opp(k)];
 #pragma unroll
@@ -452,6 +462,10 @@ struct NodeOps {
         ddrho += ws * (-0.1f / 3.0f) * P.inv_A_in;
       }
     }
+#if ALBM_ADJ_TWO_PHASE
+    asm volatile("" ::: "memory");  // keep the lambda gathers after this point
+#endif
+    load(a, b);
     // ---- scalar lattices ----
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
