@@ -302,6 +302,22 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """A few launches of each kernel on a lattice that still exceeds L2."""
+    import torch
+    from paper_1501_04741_gb300.albm import Solver
+    P = inputs.scaled(inputs.mixer3d(), (256, 128, 64), nsteps=4, obj_window=4, ckpt_every=1,
+                      precision=args.precision)
+    th = torch.from_numpy(inputs.theta_uniform(P, 0).reshape(-1)).cuda()
+    with Solver(P, th) as s:
+        s.primal_step(P.nsteps)
+        s.adjoint_step(P.nsteps)
+        J = s.objective()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "mixer3d 256x128x64", "precision": args.precision, "J": J}))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,7 +329,12 @@ def main(argv=None):
     ap.add_argument("--mem-budget", type=float, default=0.0)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the small ncu case instead: mixer3d physics on 256x128x64, "
+                         "4 primal + 4 adjoint steps (277 MB per state, > L2)")
     args = ap.parse_args(argv)
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -1,0 +1,119 @@
+"""Reduced-precision population storage (BF16 / FP16 deviations from the rest
+weights, collision in FP32, FP64 objective and gradient accumulation).
+
+Exactness where the arithmetic is the same: from a state that is already
+representable in the storage type, one primal step matches the FP64 oracle
+up to the final rounding of the output deviations to 16 bits, and one
+adjoint step (FP32 adjoint, 16-bit state) matches it to FP32 accuracy.
+
+Whole trajectories: the error against the FP64 oracle is measured and
+reported (printed), and checked against bounds that only catch gross
+breakage; the FP32 storage bars of the parity tests do not apply.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.solver import Oracle
+from paper_1501_04741_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+# unit roundoff of the stored deviations
+EPS = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}
+
+
+def _cases():
+    mix = inputs.scaled(inputs.mixer3d(), (21, 11, 10), nsteps=40, obj_window=6)
+    exch = inputs.scaled(inputs.exchanger3d(), (23, 10, 9), nsteps=40)
+    return {"mixer3d_mrt": mix, "exchanger3d_bgk": exch}
+
+
+CASES = _cases()
+
+
+def _theta(P, seed):
+    return inputs.theta_uniform(P, seed)
+
+
+def _solver(P, theta):
+    from paper_1501_04741_gb300.albm import Solver
+    return Solver(P, torch.from_numpy(theta.reshape(-1)).cuda())
+
+
+def _np(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _random_state(o, seed):
+    rng = np.random.default_rng(seed)
+    m = o.model
+    F = o.initial().clone()
+    F[:m.Q] *= torch.tensor(1 + 0.02 * rng.standard_normal(F[:m.Q].shape))
+    if m.NS:
+        F[m.Q:] = torch.tensor(0.1 * rng.random(F[m.Q:].shape))
+    return F
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_step_in_reduced_storage(name, prec):
+    P = CASES[name].replace(objective="none", precision=prec)
+    th = _theta(P, 1)
+    o = Oracle(P, th)
+    F = _random_state(o, 2)
+    M = o.model.M
+    with _solver(P, th) as s:
+        s.set_populations(torch.tensor(F.reshape(M, -1).numpy(), dtype=torch.float32,
+                                       device="cuda"))
+        f0 = _np(s.populations(0))      # the state as stored (rounded deviations)
+        s.primal_step(1)
+        post = _np(s.populations(1))
+        rng = np.random.default_rng(3)
+        lam = rng.standard_normal((M, o.n)).astype(np.float32)
+        s.adjoint_seed(torch.tensor(lam, device="cuda"))
+        s.adjoint_step(1)
+        lam0 = _np(s.adjoint())
+        grad = _np(s.gradient())
+    F0 = torch.tensor(f0).view(F.shape)
+    ref = o.collide(F0).reshape(M, -1).numpy()
+    # output deviations are rounded once to the storage type
+    dev = np.abs(ref - np.concatenate([o.model.fl.w[:, None] * np.ones((o.model.Q, 1)),
+                                       np.zeros((M - o.model.Q, 1))])).max()
+    assert np.abs(post - ref).max() <= 1.01 * EPS[prec] * dev + 1e-6 * np.abs(ref).max()
+    gF, gth = o.adjoint_step(torch.tensor(lam, dtype=torch.float64).view(F.shape), F0)
+    gF = gF.reshape(M, -1).numpy()
+    gth = gth.numpy()
+    assert np.abs(lam0 - gF).max() <= 2e-5 * np.abs(gF).max()
+    assert np.abs(grad - gth).max() <= 2e-5 * np.abs(gth).max()
+
+
+BOUNDS = {  # (populations / max|f|, J relative, gradient inf-norm relative)
+    "bf16": (2e-2, 1e-1, 3e-1),
+    "fp16": (2e-3, 1e-2, 3e-2),
+}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_trajectory_error_against_oracle(name, prec, capsys):
+    P = CASES[name].replace(precision=prec)
+    th = _theta(P, 6)
+    o = Oracle(P, th)
+    J, g, _ = o.gradient()
+    _, traj = o.primal(keep=False)
+    fN = traj[-1].reshape(o.model.M, -1).numpy()
+    g = g.reshape(-1).numpy()
+    with _solver(P, th) as s:
+        s.primal_step(P.nsteps)
+        f_gpu = _np(s.populations(0))
+        J_gpu = s.objective()
+        s.adjoint_step(P.nsteps)
+        grad = _np(s.gradient())
+    e_f = np.abs(f_gpu - fN).max() / np.abs(fN).max()
+    e_J = abs(J_gpu - J) / abs(J)
+    e_g = np.abs(grad - g).max() / np.abs(g).max()
+    with capsys.disabled():
+        print(f"\n[precision] {name} {prec}: populations {e_f:.2e}  J {e_J:.2e}  dJ/dtheta {e_g:.2e}")
+    bf, bJ, bg = BOUNDS[prec]
+    assert e_f <= bf and e_J <= bJ and e_g <= bg
