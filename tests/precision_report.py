@@ -40,10 +40,10 @@ def gpu_run(P, theta):
 def part1():
     cases = {
         "channel2d 128x64 BGK, 2000+2000": inputs.channel2d(),
-        "mixer3d 48x24x24 MRT+2 scalars, 300+300": inputs.scaled(inputs.mixer3d(), (48, 24, 24),
-                                                                 nsteps=300, obj_window=50),
-        "exchanger3d 56x28x28 BGK+T, 300+300": inputs.scaled(inputs.exchanger3d(), (56, 28, 28),
-                                                             nsteps=300),
+        "mixer3d 40x20x20 MRT+2 scalars, 1000+1000": inputs.scaled(inputs.mixer3d(), (40, 20, 20),
+                                                                   nsteps=1000, obj_window=100),
+        "exchanger3d 56x28x28 BGK+T, 1200+1200": inputs.scaled(inputs.exchanger3d(), (56, 28, 28),
+                                                               nsteps=1200),
     }
     print("| workload | storage | populations err / max|f| | J rel err | dJ/dtheta rel err (inf) |")
     print("|---|---|---|---|---|")

@@ -24,8 +24,11 @@ EPS = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}
 
 
 def _cases():
-    mix = inputs.scaled(inputs.mixer3d(), (21, 11, 10), nsteps=40, obj_window=6)
-    exch = inputs.scaled(inputs.exchanger3d(), (23, 10, 9), nsteps=40)
+    # horizons long enough for the inlet scalar to reach the outlet (x / u_in
+    # steps), so that the outlet objectives are not made of values below the
+    # FP16 normal range (6.1e-5), which it stores with coarse absolute steps
+    mix = inputs.scaled(inputs.mixer3d(), (21, 11, 10), nsteps=500, obj_window=50)
+    exch = inputs.scaled(inputs.exchanger3d(), (23, 10, 9), nsteps=300)
     return {"mixer3d_mrt": mix, "exchanger3d_bgk": exch}
 
 
@@ -58,7 +61,7 @@ def _random_state(o, seed):
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_one_step_in_reduced_storage(name, prec):
-    P = CASES[name].replace(objective="none", precision=prec)
+    P = CASES[name].replace(objective="none", precision=prec, nsteps=4)
     th = _theta(P, 1)
     o = Oracle(P, th)
     F = _random_state(o, 2)

@@ -248,3 +248,72 @@ def test_uniform_scalar_has_zero_variance():
     m = o.model
     F[m.Q:] = 0.3 * m.ws.view(-1, 1, 1, 1)
     assert abs(float(o.F_obj(F))) < 1e-15
+
+
+def _uniform_flow_state(o, U, T_of_y=None, rho=1.0):
+    """Every node at equilibrium with (rho, u = (U,0,0)) and scalar 0 at T(y)."""
+    m = o.model
+    n = o.n
+    u = torch.zeros(3, n, dtype=torch.float64)
+    u[0] = U
+    F = torch.zeros(m.M, n, dtype=torch.float64)
+    F[:m.Q] = m.feq(torch.full((n,), rho, dtype=torch.float64), u)
+    if m.NS:
+        T = torch.zeros(n, dtype=torch.float64) if T_of_y is None else T_of_y(o.y.double())
+        F[m.Q:m.Q + m.Qs] = m.geq(T, u)
+    return F.view(m.M, *o.shape)
+
+
+@pytest.mark.parametrize("T", [0.0, 0.3, 1.0])
+def test_heat_flux_and_mixing_flux_closed_forms(T):
+    # Uniform flow u = (U,0,0) at rho = 1 with a uniform scalar T: at the
+    # outlet Zou-He gives u_x = U and the outlet scalar T* = T, and at the
+    # inlet rho = (s0 + 2 s_out)/(1 - U) = 1 when u_in = U, so Delta p = 0:
+    #   Eq. exchanger:obj sum_outlet u_x T = A U T,
+    #   Eq. mixing:obj    sum_outlet u_x (1 - T^2) = A U (1 - T^2).
+    U = 0.04
+    P = inputs.scaled(inputs.exchanger3d(), (12, 7, 6), u_in=U, hot=())
+    o = Oracle(P, np.zeros(P.dims[::-1], np.float32))
+    F = _uniform_flow_state(o, U, lambda y: torch.full_like(y, T))
+    A = o.n_out
+    assert abs(float(o.F_obj(F)) - A * U * T) < 1e-13
+    Pm = P.replace(objective="mixflux")
+    om = Oracle(Pm, np.zeros(P.dims[::-1], np.float32))
+    assert abs(float(om.F_obj(F)) - A * U * (1 - T * T)) < 1e-13
+
+
+def test_heat_flux_pressure_drop_term():
+    # A uniform equilibrium state at rho_0 != 1 and u = (U,0,0) with u_in = U
+    # gives inlet rho = (s0 + 2 s_out)/(1 - U) = rho_0 (Zou-He), so the
+    # pressure term is -0.1 (rho_0 - rho_out)/3; at the outlet Zou-He gives
+    # u_x = (s0 + 2 s_out)/rho_out - 1 = rho_0 (1 + U) - 1 for rho_out = 1.
+    U, rho0 = 0.03, 1.02
+    P = inputs.scaled(inputs.exchanger3d(), (12, 7, 6), u_in=U, hot=())
+    o = Oracle(P, np.zeros(P.dims[::-1], np.float32))
+    T = 0.5
+    F = _uniform_flow_state(o, U, lambda y: torch.full_like(y, T), rho=rho0)
+    A = o.n_out
+    ux_out = rho0 * (1 + U) - 1.0
+    # outlet scalar: unknown populations at equilibrium with T* and v = u_x
+    # leave T* = T because the known ones carry equilibrium at the inlet speed U
+    m = o.model
+    Es = m.sl.E
+    known = Es[:, 0] >= 0
+    phiU = 1 + Es[:, 0] * U / m.sl.cs2
+    phi_out = 1 + Es[:, 0] * ux_out / m.sl.cs2
+    Tstar = T * float((m.sl.w * phiU)[known].sum()) / (1 - float((m.sl.w * phi_out)[~known].sum()))
+    expect = A * ux_out * Tstar - 0.1 * (rho0 - 1.0) / 3.0
+    assert abs(float(o.F_obj(F)) - expect) < 1e-13
+
+
+def test_outlet_variance_of_a_two_level_profile():
+    # Outlet scalar 0 below y = Ly/2 and 1 above, fluid at rest: the outlet
+    # variance is p (1 - p), p the fraction of outlet nodes with value 1.
+    P = inputs.scaled(inputs.mixer3d(), (10, 9, 6), obj_window=0)
+    o = Oracle(P, np.zeros(P.dims[::-1], np.float32))
+    half = P.dims[1] // 2
+    F = _uniform_flow_state(o, 0.0, lambda y: (y >= half).double())
+    out = (o.flags == 4 - 1)
+    ys = o.y[out]
+    p = float((ys >= half).double().mean())
+    assert abs(float(o.F_obj(F)) - p * (1 - p)) < 1e-14
