@@ -217,6 +217,23 @@ lbm_status lbm_profile_read(lbm_handle h, double* out);
 /* Primal steps recomputed by the checkpoint schedule since the last reset. */
 long long lbm_recompute_steps(lbm_handle h);
 
+/* Batched primal steps (SURVEY K7 / continuous batching): advance each of
+ * the n handles by up to k steps, one kernel launch per step covering every
+ * handle that has not reached its horizon (at most 64 handles per launch;
+ * larger batches are split).  The per-node arithmetic is that of
+ * lbm_primal_step, so results are bit-identical to driving each handle
+ * alone.  All handles must share lattice, collision, scalar count, storage
+ * precision and stream.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (an adjoint has
+ * started on a handle), LBM_ERR_OOM. */
+lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k);
+
+/* Batched adjoint steps: each handle that has adjoint steps left goes back
+ * up to k steps (Eq. adjoint:iteration), one launch per step for all of
+ * them; states are restored per handle by its own checkpoint schedule.  A
+ * handle whose adjoint has not started starts at its current primal time.
+ * Same requirements and errors as lbm_batch_primal_step. */
+lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k);
+
 /* Objective F(f) of one pre-collision state, evaluated without allocating
  * any device memory.  The paper has no counterpart: this entry point exists
  * for callers that cannot allocate at the point of the call - code running

@@ -33,7 +33,8 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_theta", "lbm_
            "lbm_adjoint_seed", "lbm_adjoint_time", "lbm_run", "lbm_gradient",
            "lbm_get_populations", "lbm_get_populations_at", "lbm_set_populations", "lbm_get_adjoint", "lbm_get_flags",
            "lbm_check_finite", "lbm_sizes", "lbm_last_timing", "lbm_profile",
-           "lbm_profile_read", "lbm_recompute_steps", "lbm_state_objective_noalloc",
+           "lbm_profile_read", "lbm_recompute_steps", "lbm_batch_primal_step",
+           "lbm_batch_adjoint_step", "lbm_state_objective_noalloc",
            "lbm_noalloc_last_error"]
 
 
@@ -94,6 +95,8 @@ def lib():
         L.lbm_profile_read.argtypes = [vp, C.POINTER(d)]
         L.lbm_recompute_steps.argtypes = [vp]
         L.lbm_recompute_steps.restype = C.c_longlong
+        L.lbm_batch_primal_step.argtypes = [C.POINTER(vp), i, i]
+        L.lbm_batch_adjoint_step.argtypes = [C.POINTER(vp), i, i]
         L.lbm_state_objective_noalloc.argtypes = [C.POINTER(LbmParams), vp, vp, vp, vp,
                                                   C.POINTER(d)]
         L.lbm_noalloc_last_error.argtypes = []
@@ -321,3 +324,26 @@ def state_objective_noalloc(P: Problem, f, theta, flags, stream=None) -> float:
     if code != 0:
         raise AlbmError(code, L.lbm_noalloc_last_error().decode())
     return F.value
+
+
+def _handles(solvers):
+    arr = (C.c_void_p * len(solvers))()
+    for k, s in enumerate(solvers):
+        arr[k] = s._h.value
+    return arr
+
+
+def batch_primal_step(solvers, k: int = 1):
+    """Advance every solver by up to k primal steps in batched launches."""
+    L = lib()
+    code = L.lbm_batch_primal_step(_handles(solvers), len(solvers), int(k))
+    if code != 0:
+        raise AlbmError(code, L.lbm_last_error(solvers[0]._h).decode())
+
+
+def batch_adjoint_step(solvers, k: int = 1):
+    """Run up to k adjoint steps on every solver in batched launches."""
+    L = lib()
+    code = L.lbm_batch_adjoint_step(_handles(solvers), len(solvers), int(k))
+    if code != 0:
+        raise AlbmError(code, L.lbm_last_error(solvers[0]._h).decode())

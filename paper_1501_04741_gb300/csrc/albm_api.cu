@@ -695,6 +695,147 @@ lbm_status lbm_profile_read(lbm_handle h, double* out) {
 
 long long lbm_recompute_steps(lbm_handle h) { return h ? h->recompute_steps : -1; }
 
+// ---------------------------------------------------------------------------
+// batched steps over several handles of one kernel family
+// ---------------------------------------------------------------------------
+static lbm_status batch_check(const lbm_handle* hs, int n) {
+  if (!hs || n < 1) return LBM_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return LBM_ERR_ARG;
+    if (hs[i]->ks.primal != hs[0]->ks.primal || hs[i]->stream != hs[0]->stream) {
+      hs[0]->err = "batched handles need the same lattice, collision, scalars, precision and stream";
+      return LBM_ERR_ARG;
+    }
+  }
+  return LBM_OK;
+}
+
+static lbm_status batch_launch(lbm_ctx* h0, albm::BatchArgs& args, long long blocks, bool adjoint) {
+  cudaError_t e = adjoint ? h0->ks.adjoint_batch(args, blocks, h0->stream)
+                          : h0->ks.primal_batch(args, blocks, h0->stream);
+  if (e != cudaSuccess)
+    FAIL(h0, LBM_ERR_CUDA, "batched %s launch: %s", adjoint ? "adjoint" : "primal",
+         cudaGetErrorString(e));
+  args.n = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
+  lbm_status st = batch_check(hs, n);
+  if (st) return st;
+  for (int i = 0; i < n; ++i)
+    if (hs[i]->t_adj >= 0) FAIL(hs[i], LBM_ERR_STATE, "the adjoint of this trajectory has started");
+  std::vector<int> t_begin(n);
+  for (int i = 0; i < n; ++i) t_begin[i] = hs[i]->t;
+  static thread_local albm::BatchArgs args;
+  for (int step = 0; step < k; ++step) {
+    args.n = 0;
+    long long blocks = 0;
+    std::vector<std::pair<lbm_ctx*, std::pair<int, int>>> moved;  // handle, (src, dst)
+    for (int i = 0; i < n; ++i) {
+      lbm_ctx* h = hs[i];
+      if (h->t >= h->p.nsteps) continue;  // horizon reached
+      const int src = find_buf(h, h->t);
+      int dst;
+      lbm_status s = acquire(h, &dst);
+      if (s) return s;
+      h->buf_time[dst] = -2;  // reserved until the launch is issued
+      albm::InstanceDesc& D = args.inst[args.n++];
+      memset(&D, 0, sizeof(D));
+      D.P = h->kp;
+      D.Bin = h->bufs[src];
+      D.Bout = h->bufs[dst];
+      D.theta = h->theta;
+      D.flags = h->flags;
+      D.obj = h->c[h->t] != 0.0 ? h->stats_raw + 2 * (size_t)albm::kObjSlots * (size_t)h->t : nullptr;
+      D.block_begin = blocks;
+      blocks += (h->N + albm::kBlock - 1) / albm::kBlock;
+      moved.push_back({h, {src, dst}});
+      if (args.n == albm::kMaxBatch) {
+        s = batch_launch(hs[0], args, blocks, false);
+        if (s) return s;
+        blocks = 0;
+      }
+    }
+    if (args.n > 0) {
+      lbm_status s = batch_launch(hs[0], args, blocks, false);
+      if (s) return s;
+    }
+    for (auto& m : moved) {
+      lbm_ctx* h = m.first;
+      h->buf_time[m.second.second] = h->t + 1;
+      if (h->t % h->ckpt != 0) h->buf_time[m.second.first] = -1;
+      h->t += 1;
+      if (h->t == h->p.nsteps) {
+        lbm_status s = record_final_objective(h);
+        if (s) return s;
+      }
+    }
+    if (moved.empty()) break;
+  }
+  for (int i = 0; i < n; ++i) {
+    lbm_status s = fold_stats(hs[i], t_begin[i], hs[i]->t);
+    if (s) return s;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k) {
+  lbm_status st = batch_check(hs, n);
+  if (st) return st;
+  for (int i = 0; i < n; ++i)
+    if (hs[i]->t_adj < 0) {
+      lbm_status s = adjoint_start(hs[i]);
+      if (s) return s;
+    }
+  static thread_local albm::BatchArgs args;
+  for (int step = 0; step < k; ++step) {
+    args.n = 0;
+    long long blocks = 0;
+    std::vector<lbm_ctx*> moved;
+    for (int i = 0; i < n; ++i) {
+      lbm_ctx* h = hs[i];
+      if (h->t_adj <= 0) continue;  // adjoint finished
+      const int nn = h->t_adj - 1;
+      for (size_t b = 0; b < h->bufs.size(); ++b)
+        if (h->buf_time[b] > nn) h->buf_time[b] = -1;
+      lbm_status s = ensure_state(h, nn);
+      if (s) return s;
+      albm::InstanceDesc& D = args.inst[args.n++];
+      memset(&D, 0, sizeof(D));
+      D.P = h->kp;
+      D.Bin = h->bufs[find_buf(h, nn)];
+      D.theta = h->theta;
+      D.flags = h->flags;
+      D.lam_in = h->lam[h->lam_cur];
+      D.lam_out = h->lam[1 - h->lam_cur];
+      D.grad = h->grad;
+      D.ws = (float)h->c[nn];
+      D.stat_n = (h->p.objective == LBM_OBJ_VARIANCE && h->c[nn] != 0.0) ? h->stats + 2 * (size_t)nn
+                                                                         : nullptr;
+      D.has_next = 1;
+      D.block_begin = blocks;
+      blocks += (h->N + albm::kBlock - 1) / albm::kBlock;
+      moved.push_back(h);
+      if (args.n == albm::kMaxBatch) {
+        s = batch_launch(hs[0], args, blocks, true);
+        if (s) return s;
+        blocks = 0;
+      }
+    }
+    if (args.n > 0) {
+      lbm_status s = batch_launch(hs[0], args, blocks, true);
+      if (s) return s;
+    }
+    for (lbm_ctx* h : moved) {
+      h->lam_cur = 1 - h->lam_cur;
+      h->t_adj -= 1;
+    }
+    if (moved.empty()) break;
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_run(lbm_handle h) {
   if (!h) return LBM_ERR_ARG;
   lbm_status s = do_reset(h);

@@ -143,14 +143,12 @@ struct Gather {
 // primal step: B^{n+1}(x) = W^x(f^n(x)); optional objective terms of f^n
 // ---------------------------------------------------------------------------
 template <class L, int NS, bool MRT, class S>
-__global__ void __launch_bounds__(256, ALBM_PRIMAL_MINB) primal_kernel(KParams P, const S* __restrict__ Bin,
-                                                     S* __restrict__ Bout,
-                                                     const float* __restrict__ theta,
-                                                     const uint8_t* __restrict__ flags,
-                                                     double* __restrict__ obj) {
+__device__ __forceinline__ void primal_body(const KParams& P, const S* __restrict__ Bin,
+                                            S* __restrict__ Bout, const float* __restrict__ theta,
+                                            const uint8_t* __restrict__ flags,
+                                            double* __restrict__ obj, long long idx, int block) {
   using Ops = NodeOps<L, NS, MRT>;
   constexpr int Q = Ops::Q, QS = Ops::QS, NSA = Ops::NSA;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double o1 = 0.0, o2 = 0.0;
   if (idx < P.N) {
     const Geo geo = make_geo(P, idx);
@@ -166,7 +164,17 @@ __global__ void __launch_bounds__(256, ALBM_PRIMAL_MINB) primal_kernel(KParams P
 #pragma unroll
       for (int i = 0; i < QS; ++i) st(Bout + (long long)(Q + s * QS + i) * P.N + idx, g[s][i]);
   }
-  if (obj != nullptr) block_sum2(o1, o2, obj + 2 * (blockIdx.x % kObjSlots));
+  if (obj != nullptr) block_sum2(o1, o2, obj + 2 * (block % kObjSlots));
+}
+
+template <class L, int NS, bool MRT, class S>
+__global__ void __launch_bounds__(256, ALBM_PRIMAL_MINB) primal_kernel(KParams P, const S* __restrict__ Bin,
+                                                     S* __restrict__ Bout,
+                                                     const float* __restrict__ theta,
+                                                     const uint8_t* __restrict__ flags,
+                                                     double* __restrict__ obj) {
+  primal_body<L, NS, MRT, S>(P, Bin, Bout, theta, flags, obj,
+                             (long long)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
 }
 
 // objective terms of f^n only (no state write), used for F(f^N)
@@ -198,18 +206,16 @@ __global__ void __launch_bounds__(256) objective_kernel(KParams P, const S* __re
 // adjoint step: lambda^n(x) from lambda^{n+1}(x + e_j) and f^n(x)
 // ---------------------------------------------------------------------------
 template <class L, int NS, bool MRT, class S>
-__global__ void __launch_bounds__(256, ALBM_ADJOINT_MINB) adjoint_kernel(KParams P, const float* __restrict__ lam_in,
-                                                      const S* __restrict__ Bn,
-                                                      float* __restrict__ lam_out,
-                                                      const float* __restrict__ theta,
-                                                      const uint8_t* __restrict__ flags,
-                                                      double* __restrict__ grad, float ws,
-                                                      const double* __restrict__ stat_n,
-                                                      int has_next) {
+__device__ __forceinline__ void adjoint_body(const KParams& P, const float* __restrict__ lam_in,
+                                             const S* __restrict__ Bn, float* __restrict__ lam_out,
+                                             const float* __restrict__ theta,
+                                             const uint8_t* __restrict__ flags,
+                                             double* __restrict__ grad, float ws,
+                                             const double* __restrict__ stat_n, int has_next,
+                                             long long idx) {
   using Ops = NodeOps<L, NS, MRT>;
   using LS = typename Ops::LS;
   constexpr int Q = Ops::Q, QS = Ops::QS, NSA = Ops::NSA;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= P.N) return;
   const Geo geo = make_geo(P, idx);
   float d[Q], g[NSA][QS];
@@ -247,6 +253,74 @@ __global__ void __launch_bounds__(256, ALBM_ADJOINT_MINB) adjoint_kernel(KParams
 #pragma unroll
     for (int i = 0; i < QS; ++i) st(lam_out + (long long)(Q + s * QS + i) * P.N + idx, lamg[s][i]);
   if (type == FLUID || type == INLET || type == OUTLET) grad[idx] += (double)dth;
+}
+
+template <class L, int NS, bool MRT, class S>
+__global__ void __launch_bounds__(256, ALBM_ADJOINT_MINB) adjoint_kernel(KParams P, const float* __restrict__ lam_in,
+                                                      const S* __restrict__ Bn,
+                                                      float* __restrict__ lam_out,
+                                                      const float* __restrict__ theta,
+                                                      const uint8_t* __restrict__ flags,
+                                                      double* __restrict__ grad, float ws,
+                                                      const double* __restrict__ stat_n,
+                                                      int has_next) {
+  adjoint_body<L, NS, MRT, S>(P, lam_in, Bn, lam_out, theta, flags, grad, ws, stat_n, has_next,
+                              (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// batched steps: one launch advances every instance of a batch by one step.
+// The instance table travels in the kernel's parameter space (grid
+// constant); block b belongs to the instance whose block range holds b, so
+// every block is uniform in its instance and runs exactly the per-node code
+// of the single-instance kernels (bit-identical results).
+// ---------------------------------------------------------------------------
+constexpr int kMaxBatch = 64;
+
+struct InstanceDesc {
+  KParams P;
+  const void* Bin;      // primal: state n; adjoint: state n (f^n)
+  void* Bout;           // primal: state n+1
+  const float* theta;
+  const uint8_t* flags;
+  double* obj;          // primal: objective slots of step n, or null
+  const float* lam_in;
+  float* lam_out;
+  double* grad;
+  const double* stat_n;
+  float ws;
+  int has_next;
+  long long block_begin;
+};
+
+struct BatchArgs {
+  int n;
+  InstanceDesc inst[kMaxBatch];
+};
+// kernel parameters may take up to 32764 bytes (sm_70 and newer)
+static_assert(sizeof(BatchArgs) <= 32000, "instance table exceeds the kernel parameter space");
+
+__device__ __forceinline__ int batch_instance(const BatchArgs& a) {
+  int lo = 0;
+  for (int i = 1; i < a.n; ++i)
+    if ((long long)blockIdx.x >= a.inst[i].block_begin) lo = i;
+  return lo;
+}
+
+template <class L, int NS, bool MRT, class S>
+__global__ void __launch_bounds__(256, ALBM_PRIMAL_MINB) primal_batch_kernel(const __grid_constant__ BatchArgs args) {
+  const InstanceDesc& D = args.inst[batch_instance(args)];
+  const int block = (int)((long long)blockIdx.x - D.block_begin);
+  primal_body<L, NS, MRT, S>(D.P, (const S*)D.Bin, (S*)D.Bout, D.theta, D.flags, D.obj,
+                             (long long)block * blockDim.x + threadIdx.x, block);
+}
+
+template <class L, int NS, bool MRT, class S>
+__global__ void __launch_bounds__(256, ALBM_ADJOINT_MINB) adjoint_batch_kernel(const __grid_constant__ BatchArgs args) {
+  const InstanceDesc& D = args.inst[batch_instance(args)];
+  const long long block = (long long)blockIdx.x - D.block_begin;
+  adjoint_body<L, NS, MRT, S>(D.P, D.lam_in, (const S*)D.Bin, D.lam_out, D.theta, D.flags, D.grad,
+                              D.ws, D.stat_n, D.has_next, block * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -338,6 +412,8 @@ struct KernelSet {
   cudaError_t (*exportf)(const KParams&, const StepArgs&, cudaStream_t);
   cudaError_t (*importf)(const KParams&, const StepArgs&, cudaStream_t);
   cudaError_t (*nonfinite)(const KParams&, const StepArgs&, int M, cudaStream_t);
+  cudaError_t (*primal_batch)(const BatchArgs&, long long blocks, cudaStream_t);
+  cudaError_t (*adjoint_batch)(const BatchArgs&, long long blocks, cudaStream_t);
   int storage_bytes;
 };
 
@@ -374,8 +450,17 @@ struct Launch {
     nonfinite_kernel<S><<<152 * 8, kBlock, 0, st>>>((const S*)a.Bin, (long long)M * P.N, a.count);
     return cudaGetLastError();
   }
+  static cudaError_t primal_batch(const BatchArgs& a, long long blocks, cudaStream_t st) {
+    primal_batch_kernel<L, NS, MRT, S><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t adjoint_batch(const BatchArgs& a, long long blocks, cudaStream_t st) {
+    adjoint_batch_kernel<L, NS, MRT, S><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   static KernelSet set() {
-    return KernelSet{&primal, &objective, &adjoint, &exportf, &importf, &nonfinite, (int)sizeof(S)};
+    return KernelSet{&primal, &objective, &adjoint, &exportf, &importf, &nonfinite,
+                     &primal_batch, &adjoint_batch, (int)sizeof(S)};
   }
 };
 

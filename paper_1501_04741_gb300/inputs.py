@@ -203,3 +203,55 @@ def theta_grf(p: Problem, seed: int, sigma: float = 4.0) -> np.ndarray:
 def random_state(shape, seed: int, scale: float = 1.0) -> np.ndarray:
     """Seeded float64 normal array (for duality tests and random adjoints)."""
     return np.random.default_rng(seed).standard_normal(shape) * scale
+
+
+# ---------------------------------------------------------------------------
+# Batched and served workloads
+# ---------------------------------------------------------------------------
+
+def batch_instances(count: int = 64, seed: int = 0, size_scale: float = 1.0,
+                    steps=(1000, 5000)):
+    """Seeded mixed batch: a coin picks the D2Q9 channel (config-1 geometry,
+    aspect 2:1, sizes log-uniform 64^2..1024^2 nodes) or the D3Q19 + D3Q7
+    heat exchanger (aspect 2:1:1, sizes log-uniform 48^3..192^3 nodes);
+    steps uniform in ``steps``; theta ~ U[0,1] on each design box (seed
+    ``seed + i``).  ``size_scale`` shrinks the linear sizes (tests).
+    Returns a list of (Problem, theta)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        steps_i = int(rng.integers(steps[0], steps[1] + 1))
+        if rng.random() < 0.5:
+            area = math.exp(rng.uniform(math.log(64 ** 2), math.log(1024 ** 2)))
+            Ly = max(8, int(round(math.sqrt(area / 2.0) * size_scale)))
+            P = scaled(channel2d(), (2 * Ly, Ly, 1), nsteps=steps_i)
+        else:
+            vol = math.exp(rng.uniform(math.log(48 ** 3), math.log(192 ** 3)))
+            m = max(8, int(round((vol / 2.0) ** (1.0 / 3.0) * size_scale)))
+            P = scaled(exchanger3d(), (2 * m, m, m), nsteps=steps_i)
+        out.append((P, theta_uniform(P, seed + i)))
+    return out
+
+
+def serving_requests(count: int, rate: float, seed: int = 0, node_range=(1e4, 3e7),
+                     steps=(500, 5000)):
+    """Poisson-arriving sensitivity requests: arrival times (s) with mean
+    rate ``rate``/s; D2Q9 channel or D3Q19 heat exchanger at 50/50; node
+    counts log-uniform in ``node_range`` factored to aspect 2:1 (2D) or
+    2:1:1 (3D); steps uniform in ``steps``.  Returns a list of
+    (arrival_s, Problem, theta)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        nodes = math.exp(rng.uniform(math.log(node_range[0]), math.log(node_range[1])))
+        steps_i = int(rng.integers(steps[0], steps[1] + 1))
+        if rng.random() < 0.5:
+            Ly = max(8, int(round(math.sqrt(nodes / 2.0))))
+            P = scaled(channel2d(), (2 * Ly, Ly, 1), nsteps=steps_i)
+        else:
+            m = max(8, int(round((nodes / 2.0) ** (1.0 / 3.0))))
+            P = scaled(exchanger3d(), (2 * m, m, m), nsteps=steps_i)
+        out.append((t, P, theta_uniform(P, seed * 100003 + i)))
+    return out

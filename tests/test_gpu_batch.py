@@ -1,0 +1,96 @@
+"""Batched launches (one kernel per step for many instances) give results
+bit-identical to driving each instance alone, for uneven sizes and horizons,
+for batches split above the 64-instance table, and for the checkpoint
+schedule running under them."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1501_04741_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _family_2d(k):
+    rng = np.random.default_rng(k)
+    out = []
+    for i in range(k):
+        Lx = int(rng.integers(12, 70))
+        Ly = int(rng.integers(8, 40))
+        n = int(rng.integers(20, 90))
+        P = inputs.channel2d(dims=(Lx, Ly, 1), design=(Lx // 4, 3 * Lx // 4, Ly // 4, 3 * Ly // 4, 0, 1),
+                             nsteps=n, force=(1e-4, 0, 0))
+        out.append(P)
+    return out
+
+
+def _family_3d(k):
+    rng = np.random.default_rng(100 + k)
+    out = []
+    for i in range(k):
+        d = (int(rng.integers(12, 30)), int(rng.integers(8, 16)), int(rng.integers(8, 14)))
+        out.append(inputs.scaled(inputs.exchanger3d(), d, nsteps=int(rng.integers(15, 60))))
+    return out
+
+
+def _alone(P, th, **kw):
+    from paper_1501_04741_gb300.albm import Solver
+    with Solver(P, torch.from_numpy(th.reshape(-1)).cuda(), **kw) as s:
+        s.run()
+        return s.objective(), s.gradient().cpu().numpy()
+
+
+def _batched(Ps, ths, **kw):
+    from paper_1501_04741_gb300.albm import Solver, batch_adjoint_step, batch_primal_step
+    ss = [Solver(P, torch.from_numpy(th.reshape(-1)).cuda(), **kw) for P, th in zip(Ps, ths)]
+    try:
+        horizon = max(P.nsteps for P in Ps)
+        batch_primal_step(ss, horizon)
+        for s, P in zip(ss, Ps):
+            assert s.time == P.nsteps
+        Js = [s.objective() for s in ss]
+        batch_adjoint_step(ss, horizon)
+        for s in ss:
+            assert s.adjoint_time == 0
+        gs = [s.gradient().cpu().numpy() for s in ss]
+        return Js, gs
+    finally:
+        for s in ss:
+            s.close()
+
+
+@pytest.mark.parametrize("family", ["2d", "3d"])
+def test_batched_equals_alone(family):
+    Ps = _family_2d(7) if family == "2d" else _family_3d(5)
+    ths = [inputs.theta_uniform(P, i) for i, P in enumerate(Ps)]
+    Js, gs = _batched(Ps, ths)
+    for P, th, J, g in zip(Ps, ths, Js, gs):
+        J1, g1 = _alone(P, th)
+        assert J == J1
+        assert np.array_equal(g, g1)
+
+
+def test_batch_split_beyond_table_and_small_pools():
+    Ps = _family_2d(70)
+    ths = [inputs.theta_uniform(P, i) for i, P in enumerate(Ps)]
+    # a small pool per instance so that the recompute schedule runs too
+    kw = dict(mem_budget=0)
+    Js, gs = _batched(Ps[:70], ths[:70])
+    for i in (0, 33, 64, 69):
+        J1, g1 = _alone(Ps[i], ths[i])
+        assert Js[i] == J1 and np.array_equal(gs[i], g1)
+    Pc = [P.replace(ckpt_every=7) for P in Ps[:6]]
+    budgets = [8 * 4 * 9 * P.n_nodes for P in Pc]
+    from paper_1501_04741_gb300.albm import Solver, batch_adjoint_step, batch_primal_step
+    ss = [Solver(P, torch.from_numpy(th.reshape(-1)).cuda(), mem_budget=b)
+          for P, th, b in zip(Pc, ths[:6], budgets)]
+    try:
+        batch_primal_step(ss, 100)
+        batch_adjoint_step(ss, 100)
+        for s, P, th in zip(ss, Pc, ths[:6]):
+            assert s.recompute_steps() > 0
+            J1, g1 = _alone(P, th)
+            assert s.objective() == J1 and np.array_equal(s.gradient().cpu().numpy(), g1)
+    finally:
+        for s in ss:
+            s.close()
