@@ -302,6 +302,84 @@ def run_ours(args):
     return 0
 
 
+def run_batch64(args):
+    """Config 4: 64 seeded D2Q9 / D3Q19 instances (sizes log-uniform, 1000-5000
+    steps) through the batched torch.autograd.Function, against the same
+    instances one at a time through the single-instance Function."""
+    import torch
+    from paper_1501_04741_gb300.albm import Solver
+    from paper_1501_04741_gb300.autograd import albm_objective, albm_objectives
+    batch = inputs.batch_instances(args.count or 64, seed=0, size_scale=args.size_scale)
+    free, _ = torch.cuda.mem_get_info()
+    sizes = [P.n_nodes * (9 if P.lattice == "D2Q9" else 26) * 4 for P, _ in batch]
+    budget = 0.6 * free
+    stream = torch.cuda.Stream()
+    solvers, thetas = [], []
+    for (P, th), sz in zip(batch, sizes):
+        t = torch.from_numpy(th.reshape(-1)).cuda().requires_grad_(True)
+        thetas.append(t)
+        solvers.append(Solver(P, t.detach(), stream=stream,
+                              mem_budget=max(8 * sz, budget * sz / sum(sizes))))
+    updates = sum(2.0 * P.n_nodes * P.nsteps for P, _ in batch)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Js = albm_objectives(thetas, solvers)
+    Js.sum().backward()
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    g_batch = [t.grad.clone() for t in thetas]
+    for t in thetas:
+        t.grad = None
+    t0 = time.perf_counter()
+    for t, s in zip(thetas, solvers):
+        albm_objective(t, s).backward()
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    same = all(torch.equal(a, t.grad) for a, t in zip(g_batch, thetas))
+    for s in solvers:
+        s.close()
+    print(json.dumps({
+        "metric": "batched autograd primal+adjoint MLUPS", "workload": "batch64",
+        "value": updates / t_batch / 1e6, "unit": UNIT, "higher_is_better": True,
+        "instances": len(batch), "nodes_total": sum(P.n_nodes for P, _ in batch),
+        "d2q9": sum(P.lattice == "D2Q9" for P, _ in batch),
+        "batched_s": t_batch, "one_at_a_time_s": t_seq,
+        "one_at_a_time_MLUPS": updates / t_seq / 1e6,
+        "gradients_identical": bool(same), "size_scale": args.size_scale}), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Config 5: Poisson-arriving sensitivity requests (D2Q9 or D3Q19 at
+    50/50, 1e4..3e7 nodes log-uniform, 500..5000 steps), served with
+    continuous batching, against one-at-a-time plain FP32 solves."""
+    import torch
+    from paper_1501_04741_gb300.serve import Request, Server, run_sequential
+    rates = [float(r) for r in args.rates.split(",")]
+    rows = []
+    for rate in rates:
+        spec = inputs.serving_requests(args.count or 12, rate=rate, seed=int(rate * 10),
+                                       node_range=(1e4, args.max_nodes))
+        reqs = [Request(i, t, P, th) for i, (t, P, th) in enumerate(spec)]
+        srv = Server(steps_per_tick=args.tick, keep_gradients=False)
+        st = srv.run(reqs)
+        torch.cuda.synchronize()
+        seq = [Request(i, t, P, th) for i, (t, P, th) in enumerate(spec)]
+        sq = run_sequential(seq, keep_gradients=False)
+        same = all(a.J == b.J for a, b in zip(reqs, seq))
+        row = {"rate_per_s": rate, "requests": len(reqs),
+               "batched": {"p50_s": st.p50, "p99_s": st.p99, "MLUPS": st.mlups,
+                           "makespan_s": st.makespan, "max_resident": st.max_resident},
+               "one_at_a_time": {"p50_s": sq.p50, "p99_s": sq.p99, "MLUPS": sq.mlups,
+                                 "makespan_s": sq.makespan},
+               "J_identical": bool(same)}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"metric": "served p50/p99 vs one-at-a-time FP32", "workload": "serve",
+                      "max_nodes": args.max_nodes, "rows": rows}), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """A few launches of each kernel on a lattice that still exceeds L2."""
     import torch
@@ -329,12 +407,22 @@ def main(argv=None):
     ap.add_argument("--mem-budget", type=float, default=0.0)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="mixer3d", choices=["mixer3d", "batch64", "serve"])
+    ap.add_argument("--count", type=int, default=0, help="instances (batch64) or requests (serve)")
+    ap.add_argument("--size-scale", type=float, default=1.0, help="batch64: linear size factor")
+    ap.add_argument("--rates", default="2,20,200", help="serve: arrival rates per second")
+    ap.add_argument("--max-nodes", type=float, default=3e7, help="serve: largest request")
+    ap.add_argument("--tick", type=int, default=20, help="serve: steps per batched tick")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the small ncu case instead: mixer3d physics on 256x128x64, "
                          "4 primal + 4 adjoint steps (277 MB per state, > L2)")
     args = ap.parse_args(argv)
     if args.profile_case:
         return run_profile_case(args)
+    if args.workload == "batch64":
+        return run_batch64(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
