@@ -336,6 +336,8 @@ def run_batch64(args):
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     same = all(torch.equal(a, t.grad) for a, t in zip(g_batch, thetas))
+    gdiff = max(float((a.double() - t.grad.double()).abs().max() / t.grad.double().abs().max().clamp_min(1e-300))
+                for a, t in zip(g_batch, thetas))
     for s in solvers:
         s.close()
     print(json.dumps({
@@ -345,7 +347,8 @@ def run_batch64(args):
         "d2q9": sum(P.lattice == "D2Q9" for P, _ in batch),
         "batched_s": t_batch, "one_at_a_time_s": t_seq,
         "one_at_a_time_MLUPS": updates / t_seq / 1e6,
-        "gradients_identical": bool(same), "size_scale": args.size_scale}), flush=True)
+        "gradients_identical": bool(same), "gradient_max_rel_diff": gdiff,
+        "size_scale": args.size_scale}), flush=True)
     return 0
 
 
@@ -367,12 +370,13 @@ def run_serve(args):
         seq = [Request(i, t, P, th) for i, (t, P, th) in enumerate(spec)]
         sq = run_sequential(seq, keep_gradients=False)
         same = all(a.J == b.J for a, b in zip(reqs, seq))
+        jdiff = max(abs(a.J - b.J) / max(abs(b.J), 1e-300) for a, b in zip(reqs, seq))
         row = {"rate_per_s": rate, "requests": len(reqs),
                "batched": {"p50_s": st.p50, "p99_s": st.p99, "MLUPS": st.mlups,
                            "makespan_s": st.makespan, "max_resident": st.max_resident},
                "one_at_a_time": {"p50_s": sq.p50, "p99_s": sq.p99, "MLUPS": sq.mlups,
                                  "makespan_s": sq.makespan},
-               "J_identical": bool(same)}
+               "J_identical": bool(same), "J_max_rel_diff": jdiff}
         rows.append(row)
         print(json.dumps(row), flush=True)
     print(json.dumps({"metric": "served p50/p99 vs one-at-a-time FP32", "workload": "serve",

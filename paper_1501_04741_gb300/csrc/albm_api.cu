@@ -44,8 +44,9 @@ struct lbm_ctx {
   uint8_t* flags = nullptr;
   float* theta = nullptr;
   double* grad = nullptr;
-  double* stats = nullptr;          // 2 doubles per step 0..nsteps (folded)
-  double* stats_raw = nullptr;      // kObjSlots pairs per step (accumulated)
+  double* stats = nullptr;          // 2 doubles per step 0..nsteps
+  double* partials = nullptr;       // 2 doubles per block of one launch
+  long long nblocks = 0;
   unsigned long long* counter = nullptr;
   float* lam[2] = {nullptr, nullptr};
   int lam_cur = 0;
@@ -210,19 +211,55 @@ static StepArgs blank_args(lbm_ctx* h) {
   return a;
 }
 
+namespace albm {
+__global__ void __launch_bounds__(256) fold_partials_kernel(const double* __restrict__ partials,
+                                                            long long nblocks,
+                                                            double* __restrict__ out) {
+  __shared__ double sh[2][256];
+  double a = 0.0, b = 0.0;
+  for (long long i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = b;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sh[0][0];
+    out[1] = sh[1][0];
+  }
+}
+}  // namespace albm
+
+// fold the per-block partials of step t into the objective record
+static lbm_status fold_objective(lbm_ctx* h, int t) {
+  albm::fold_partials_kernel<<<1, 256, 0, h->stream>>>(h->partials, h->nblocks,
+                                                        h->stats + 2 * (size_t)t);
+  h->launches_other++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "objective fold launch: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
 // one primal step from the state kept at time t (buffer src) into buffer dst
 static lbm_status launch_primal(lbm_ctx* h, int src, int dst, int t, bool record, int kind) {
   StepArgs a = blank_args(h);
   a.Bin = h->bufs[src];
   a.Bout = h->bufs[dst];
-  a.obj = (record && t <= h->p.nsteps && h->c[t] != 0.0)
-              ? h->stats_raw + 2 * (size_t)albm::kObjSlots * (size_t)t
-              : nullptr;
+  a.obj = (record && t <= h->p.nsteps && h->c[t] != 0.0) ? h->partials : nullptr;
   int slot;
   prof_begin(h, kind, &slot);
   cudaError_t e = h->ks.primal(h->kp, a, h->stream);
   prof_end(h, slot);
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "primal kernel launch: %s", cudaGetErrorString(e));
+  if (a.obj) return fold_objective(h, t);
   return LBM_OK;
 }
 
@@ -231,11 +268,11 @@ static lbm_status record_final_objective(lbm_ctx* h) {
   if (t > h->p.nsteps || h->c[t] == 0.0 || h->p.objective == LBM_OBJ_NONE) return LBM_OK;
   StepArgs a = blank_args(h);
   a.Bin = h->bufs[find_buf(h, t)];
-  a.obj = h->stats_raw + 2 * (size_t)albm::kObjSlots * (size_t)t;
+  a.obj = h->partials;
   cudaError_t e = h->ks.objective(h->kp, a, h->stream);
   h->launches_other++;
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "objective kernel launch: %s", cudaGetErrorString(e));
-  return LBM_OK;
+  return fold_objective(h, t);
 }
 
 // make f^n available in the pool (recompute from the latest kept state < n)
@@ -328,32 +365,6 @@ static lbm_status do_reset(lbm_ctx* h) {
   h->t_adj = -1;
   h->recompute_steps = 0;
   CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * 2 * (size_t)(h->p.nsteps + 1), h->stream));
-  CK(h, cudaMemsetAsync(h->stats_raw, 0,
-                        sizeof(double) * 2 * albm::kObjSlots * (size_t)(h->p.nsteps + 1), h->stream));
-  return LBM_OK;
-}
-
-namespace albm {
-// stats[n][k] = sum over slots of raw[n][slot][k], n in [n0, n1]
-__global__ void fold_stats_kernel(const double* __restrict__ raw, double* __restrict__ stats,
-                                  int n0, int n1) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = n0 + i / 2, k = i % 2;
-  if (n > n1) return;
-  double acc = 0.0;
-  for (int s = 0; s < kObjSlots; ++s) acc += raw[((long long)n * kObjSlots + s) * 2 + k];
-  stats[2 * (long long)n + k] = acc;
-}
-}  // namespace albm
-
-// fold the slot accumulators of steps n0..n1 into the per-step record
-static lbm_status fold_stats(lbm_ctx* h, int n0, int n1) {
-  if (n1 < n0 || h->p.objective == LBM_OBJ_NONE) return LBM_OK;
-  const int threads = 2 * (n1 - n0 + 1);
-  albm::fold_stats_kernel<<<(threads + 255) / 256, 256, 0, h->stream>>>(h->stats_raw, h->stats,
-                                                                          n0, n1);
-  h->launches_other++;
-  CK(h, cudaGetLastError());
   return LBM_OK;
 }
 
@@ -474,7 +485,8 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   CKC(cudaMalloc(&h->theta, sizeof(float) * (size_t)h->N));
   CKC(cudaMalloc(&h->grad, sizeof(double) * (size_t)h->N));
   CKC(cudaMalloc(&h->stats, sizeof(double) * 2 * (size_t)(p.nsteps + 1)));
-  CKC(cudaMalloc(&h->stats_raw, sizeof(double) * 2 * albm::kObjSlots * (size_t)(p.nsteps + 1)));
+  h->nblocks = (h->N + albm::kBlock - 1) / albm::kBlock;
+  CKC(cudaMalloc(&h->partials, sizeof(double) * 2 * (size_t)h->nblocks));
   CKC(cudaMalloc(&h->counter, sizeof(unsigned long long)));
   CKC(cudaMalloc(&h->lam[0], sizeof(float) * (size_t)h->M * (size_t)h->N));
   CKC(cudaMalloc(&h->lam[1], sizeof(float) * (size_t)h->M * (size_t)h->N));
@@ -532,7 +544,7 @@ void lbm_destroy(lbm_handle h) {
   cudaFree(h->theta);
   cudaFree(h->grad);
   cudaFree(h->stats);
-  cudaFree(h->stats_raw);
+  cudaFree(h->partials);
   cudaFree(h->counter);
   cudaFree(h->lam[0]);
   cudaFree(h->lam[1]);
@@ -566,7 +578,6 @@ lbm_status lbm_primal_step(lbm_handle h, int k) {
          h->p.nsteps);
   if (h->t_adj >= 0) FAIL(h, LBM_ERR_STATE, "the adjoint of this trajectory has started; reset first");
   CK(h, cudaEventRecord(h->t0, h->stream));
-  const int t_begin = h->t;
   for (int i = 0; i < k; ++i) {
     const int src = find_buf(h, h->t);
     int dst;
@@ -580,10 +591,6 @@ lbm_status lbm_primal_step(lbm_handle h, int k) {
   }
   if (k > 0 && h->t == h->p.nsteps) {
     lbm_status s = record_final_objective(h);
-    if (s) return s;
-  }
-  if (k > 0) {
-    lbm_status s = fold_stats(h, t_begin, h->t);
     if (s) return s;
   }
   CK(h, cudaEventRecord(h->t1, h->stream));
@@ -710,6 +717,12 @@ static lbm_status batch_check(const lbm_handle* hs, int n) {
   return LBM_OK;
 }
 
+// report a member's failure on the first handle, which the caller queries
+static lbm_status batch_fail(lbm_ctx* h0, lbm_ctx* h, lbm_status code) {
+  if (h != h0) h0->err = std::string("batched handle: ") + h->err;
+  return code;
+}
+
 static lbm_status batch_launch(lbm_ctx* h0, albm::BatchArgs& args, long long blocks, bool adjoint) {
   cudaError_t e = adjoint ? h0->ks.adjoint_batch(args, blocks, h0->stream)
                           : h0->ks.primal_batch(args, blocks, h0->stream);
@@ -725,8 +738,6 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
   if (st) return st;
   for (int i = 0; i < n; ++i)
     if (hs[i]->t_adj >= 0) FAIL(hs[i], LBM_ERR_STATE, "the adjoint of this trajectory has started");
-  std::vector<int> t_begin(n);
-  for (int i = 0; i < n; ++i) t_begin[i] = hs[i]->t;
   static thread_local albm::BatchArgs args;
   for (int step = 0; step < k; ++step) {
     args.n = 0;
@@ -738,7 +749,7 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
       const int src = find_buf(h, h->t);
       int dst;
       lbm_status s = acquire(h, &dst);
-      if (s) return s;
+      if (s) return batch_fail(hs[0], h, s);
       h->buf_time[dst] = -2;  // reserved until the launch is issued
       albm::InstanceDesc& D = args.inst[args.n++];
       memset(&D, 0, sizeof(D));
@@ -747,7 +758,7 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
       D.Bout = h->bufs[dst];
       D.theta = h->theta;
       D.flags = h->flags;
-      D.obj = h->c[h->t] != 0.0 ? h->stats_raw + 2 * (size_t)albm::kObjSlots * (size_t)h->t : nullptr;
+      D.obj = h->c[h->t] != 0.0 ? h->partials : nullptr;
       D.block_begin = blocks;
       blocks += (h->N + albm::kBlock - 1) / albm::kBlock;
       moved.push_back({h, {src, dst}});
@@ -763,19 +774,19 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
     }
     for (auto& m : moved) {
       lbm_ctx* h = m.first;
+      if (h->c[h->t] != 0.0) {
+        lbm_status s = fold_objective(h, h->t);
+        if (s) return batch_fail(hs[0], h, s);
+      }
       h->buf_time[m.second.second] = h->t + 1;
       if (h->t % h->ckpt != 0) h->buf_time[m.second.first] = -1;
       h->t += 1;
       if (h->t == h->p.nsteps) {
         lbm_status s = record_final_objective(h);
-        if (s) return s;
+        if (s) return batch_fail(hs[0], h, s);
       }
     }
     if (moved.empty()) break;
-  }
-  for (int i = 0; i < n; ++i) {
-    lbm_status s = fold_stats(hs[i], t_begin[i], hs[i]->t);
-    if (s) return s;
   }
   return LBM_OK;
 }
@@ -786,7 +797,7 @@ lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k) {
   for (int i = 0; i < n; ++i)
     if (hs[i]->t_adj < 0) {
       lbm_status s = adjoint_start(hs[i]);
-      if (s) return s;
+      if (s) return batch_fail(hs[0], hs[i], s);
     }
   static thread_local albm::BatchArgs args;
   for (int step = 0; step < k; ++step) {
@@ -800,7 +811,7 @@ lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k) {
       for (size_t b = 0; b < h->bufs.size(); ++b)
         if (h->buf_time[b] > nn) h->buf_time[b] = -1;
       lbm_status s = ensure_state(h, nn);
-      if (s) return s;
+      if (s) return batch_fail(hs[0], h, s);
       albm::InstanceDesc& D = args.inst[args.n++];
       memset(&D, 0, sizeof(D));
       D.P = h->kp;
@@ -913,8 +924,6 @@ lbm_status lbm_set_populations(lbm_handle h, const float* src) {
   h->t = 0;
   h->t_adj = -1;
   CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * 2 * (size_t)(h->p.nsteps + 1), h->stream));
-  CK(h, cudaMemsetAsync(h->stats_raw, 0,
-                        sizeof(double) * 2 * albm::kObjSlots * (size_t)(h->p.nsteps + 1), h->stream));
   return LBM_OK;
 }
 

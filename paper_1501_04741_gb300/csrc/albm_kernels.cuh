@@ -84,13 +84,12 @@ __device__ __forceinline__ Geo make_geo(const KParams& P, long long idx) {
   return g;
 }
 
-// Per-step objective sums are spread over kObjSlots accumulator pairs (block
-// index modulo kObjSlots) so that the blocks of one launch do not all
-// serialise on one address; fold_stats_kernel adds the slots afterwards.
-constexpr int kObjSlots = 64;
-
-// ---- block reduction of two doubles into global accumulators -------------
-__device__ __forceinline__ void block_sum2(double a, double b, double* out) {
+// ---- deterministic objective reduction ------------------------------------
+// Each block writes the sums of its nodes' objective terms to its own slot
+// of a partials array (plain stores: every slot is rewritten on each use, so
+// nothing needs clearing); fold_partials_kernel then adds the slots in a
+// fixed order.  J is therefore bit-reproducible, alone or batched.
+__device__ __forceinline__ void block_partial2(double a, double b, double* out) {
   __shared__ double sa[32], sb[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -113,11 +112,16 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* out) {
       b += __shfl_down_sync(0xffffffffu, b, o);
     }
     if (lane == 0) {
-      if (a != 0.0) atomicAdd(out, a);
-      if (b != 0.0) atomicAdd(out + 1, b);
+      out[0] = a;
+      out[1] = b;
     }
   }
 }
+
+// out[k] = sum over blocks of partials[2 b + k], one block, fixed order
+__global__ void __launch_bounds__(256) fold_partials_kernel(const double* __restrict__ partials,
+                                                            long long nblocks,
+                                                            double* __restrict__ out);
 
 template <class L, int NS, class S>
 struct Gather {
@@ -164,7 +168,7 @@ __device__ __forceinline__ void primal_body(const KParams& P, const S* __restric
 #pragma unroll
       for (int i = 0; i < QS; ++i) st(Bout + (long long)(Q + s * QS + i) * P.N + idx, g[s][i]);
   }
-  if (obj != nullptr) block_sum2(o1, o2, obj + 2 * (block % kObjSlots));
+  if (obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
 }
 
 template <class L, int NS, bool MRT, class S>
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(256) objective_kernel(KParams P, const S* __re
       Ops::forward(P, type, theta[idx], geo.y, d, g, true, o1, o2);
     }
   }
-  block_sum2(o1, o2, obj + 2 * (blockIdx.x % kObjSlots));
+  block_partial2(o1, o2, obj + 2 * (long long)blockIdx.x);
 }
 
 
@@ -283,7 +287,7 @@ struct InstanceDesc {
   void* Bout;           // primal: state n+1
   const float* theta;
   const uint8_t* flags;
-  double* obj;          // primal: objective slots of step n, or null
+  double* obj;          // primal: per-block objective partials, or null
   const float* lam_in;
   float* lam_out;
   double* grad;

@@ -61,7 +61,7 @@ def _random_state(o, seed):
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_one_step_in_reduced_storage(name, prec):
-    P = CASES[name].replace(objective="none", precision=prec, nsteps=4)
+    P = CASES[name].replace(objective="none", precision=prec, nsteps=4, obj_window=0)
     th = _theta(P, 1)
     o = Oracle(P, th)
     F = _random_state(o, 2)
