@@ -311,7 +311,7 @@ def run_batch64(args):
     from paper_1501_04741_gb300.autograd import albm_objective, albm_objectives
     batch = inputs.batch_instances(args.count or 64, seed=0, size_scale=args.size_scale)
     free, _ = torch.cuda.mem_get_info()
-    sizes = [P.n_nodes * (9 if P.lattice == "D2Q9" else 26) * 4 for P, _ in batch]
+    sizes = [P.n_nodes * (9 if P.lattice == "D2Q9" else 33) * 4 for P, _ in batch]
     budget = 0.6 * free
     stream = torch.cuda.Stream()
     solvers, thetas = [], []
@@ -335,6 +335,7 @@ def run_batch64(args):
         albm_objective(t, s).backward()
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
+    finite = all(bool(torch.isfinite(t.grad).all()) for t in thetas)
     same = all(torch.equal(a, t.grad) for a, t in zip(g_batch, thetas))
     gdiff = max(float((a.double() - t.grad.double()).abs().max() / t.grad.double().abs().max().clamp_min(1e-300))
                 for a, t in zip(g_batch, thetas))
@@ -348,6 +349,7 @@ def run_batch64(args):
         "batched_s": t_batch, "one_at_a_time_s": t_seq,
         "one_at_a_time_MLUPS": updates / t_seq / 1e6,
         "gradients_identical": bool(same), "gradient_max_rel_diff": gdiff,
+        "gradients_finite": finite,
         "size_scale": args.size_scale}), flush=True)
     return 0
 

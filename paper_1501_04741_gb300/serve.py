@@ -175,9 +175,12 @@ class Server:
             s = r.solver
             if s.adjoint_time == 0:
                 r.J = s.objective()
+                g = s.gradient()
+                g = g.cpu().numpy() if hasattr(g, "cpu") else np.asarray(g)
+                if not (np.isfinite(r.J) and np.isfinite(g).all()):
+                    r.error = "non-finite objective or gradient"   # watchdog
                 if self.keep_gradients:
-                    g = s.gradient()
-                    r.grad = g.cpu().numpy() if hasattr(g, "cpu") else np.asarray(g)
+                    r.grad = g
                 r.done = time.perf_counter() - self._t0
                 s.close()
                 r.solver = None
@@ -256,8 +259,11 @@ def run_sequential(requests, stream=None, keep_gradients: bool = True) -> ServeS
             with Solver(r.P, r.theta, stream=stream) as s:
                 s.run()
                 r.J = s.objective()
+                g = s.gradient().cpu().numpy()
+                if not (np.isfinite(r.J) and np.isfinite(g).all()):
+                    r.error = "non-finite objective or gradient"
                 if keep_gradients:
-                    r.grad = s.gradient().cpu().numpy()
+                    r.grad = g
         except (AlbmError, RuntimeError) as e:
             r.error = str(e)
         r.done = time.perf_counter() - t0
