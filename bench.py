@@ -311,7 +311,7 @@ def run_batch64(args):
     from paper_1501_04741_gb300.autograd import albm_objective, albm_objectives
     batch = inputs.batch_instances(args.count or 64, seed=0, size_scale=args.size_scale)
     free, _ = torch.cuda.mem_get_info()
-    sizes = [P.n_nodes * (9 if P.lattice == "D2Q9" else 33) * 4 for P, _ in batch]
+    sizes = [P.n_nodes * (9 if P.lattice == "D2Q9" else 19) * 4 for P, _ in batch]
     budget = 0.6 * free
     stream = torch.cuda.Stream()
     solvers, thetas = [], []
@@ -418,7 +418,7 @@ def main(argv=None):
     ap.add_argument("--size-scale", type=float, default=1.0, help="batch64: linear size factor")
     ap.add_argument("--rates", default="2,20,200", help="serve: arrival rates per second")
     ap.add_argument("--max-nodes", type=float, default=3e7, help="serve: largest request")
-    ap.add_argument("--tick", type=int, default=20, help="serve: steps per batched tick")
+    ap.add_argument("--tick", type=int, default=200, help="serve: most steps per request per tick")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the small ncu case instead: mixer3d physics on 256x128x64, "
                          "4 primal + 4 adjoint steps (277 MB per state, > L2)")

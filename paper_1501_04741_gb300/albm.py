@@ -166,6 +166,7 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._params = make_params(P, mem_budget)
         th = self._as_f32(theta)
+        self._sync_in()
         fl = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8)
         code = self._L.lbm_create(C.byref(self._h), C.byref(self._params), _ptr(th),
                                   None if fl is None else _ptr(fl), _stream_ptr(self.stream))
@@ -181,6 +182,24 @@ class Solver:
         self.M, self.N = M.value, N.value
 
     # ---- helpers ---------------------------------------------------------------
+    # The library works on the solver's stream; torch tensors are produced and
+    # consumed on torch's current stream.  Device inputs are made visible to
+    # the solver's stream before a call reads them, and device outputs to the
+    # current stream after a call writes them.
+    def _sync_in(self):
+        import torch
+        if isinstance(self.stream, torch.cuda.Stream):
+            cur = torch.cuda.current_stream()
+            if self.stream != cur:
+                self.stream.wait_stream(cur)
+
+    def _sync_out(self):
+        import torch
+        if isinstance(self.stream, torch.cuda.Stream):
+            cur = torch.cuda.current_stream()
+            if self.stream != cur:
+                cur.wait_stream(self.stream)
+
     def _as_f32(self, theta):
         import torch
         if isinstance(theta, torch.Tensor):
@@ -212,7 +231,9 @@ class Solver:
 
     # ---- the C ABI --------------------------------------------------------------
     def set_theta(self, theta):
-        self._check(self._L.lbm_set_theta(self._h, _ptr(self._as_f32(theta))))
+        th = self._as_f32(theta)
+        self._sync_in()
+        self._check(self._L.lbm_set_theta(self._h, _ptr(th)))
 
     def reset(self):
         self._check(self._L.lbm_reset(self._h))
@@ -224,6 +245,7 @@ class Solver:
         self._check(self._L.lbm_adjoint_step(self._h, int(k)))
 
     def adjoint_seed(self, lam):
+        self._sync_in()
         self._check(self._L.lbm_adjoint_seed(self._h, _ptr(lam)))
 
     def run(self):
@@ -247,7 +269,9 @@ class Solver:
         import torch
         if out is None:
             out = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        self._sync_in()
         self._check(self._L.lbm_gradient(self._h, _ptr(out)))
+        self._sync_out()
         return out
 
     def populations(self, which: int = 0, out=None):
@@ -255,7 +279,9 @@ class Solver:
         import torch
         if out is None:
             out = torch.empty((self.M, self.N), dtype=torch.float32, device="cuda")
+        self._sync_in()
         self._check(self._L.lbm_get_populations(self._h, _ptr(out), int(which)))
+        self._sync_out()
         return out
 
     def populations_at(self, time: int, which: int = 0, out=None):
@@ -263,17 +289,22 @@ class Solver:
         import torch
         if out is None:
             out = torch.empty((self.M, self.N), dtype=torch.float32, device="cuda")
+        self._sync_in()
         self._check(self._L.lbm_get_populations_at(self._h, int(time), _ptr(out), int(which)))
+        self._sync_out()
         return out
 
     def set_populations(self, f):
+        self._sync_in()
         self._check(self._L.lbm_set_populations(self._h, _ptr(f)))
 
     def adjoint(self, out=None):
         import torch
         if out is None:
             out = torch.empty((self.M, self.N), dtype=torch.float32, device="cuda")
+        self._sync_in()
         self._check(self._L.lbm_get_adjoint(self._h, _ptr(out)))
+        self._sync_out()
         return out
 
     def flags(self) -> np.ndarray:

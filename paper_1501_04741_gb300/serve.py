@@ -44,16 +44,22 @@ def densities(P: Problem) -> int:
     return Q_FLUID[P.lattice] + P.nscalars * Q_SCALAR[P.lattice]
 
 
-def pool_states(P: Problem, max_states: int = 48) -> int:
-    """States the request's pool may hold: all of them when the trajectory
-    is short, else ``max_states`` (level-1 checkpoints plus recompute)."""
-    return int(min(P.nsteps + 2, max(8, max_states)))
+def state_bytes(P: Problem) -> int:
+    return densities(P) * P.n_nodes * STORAGE[P.precision]
 
 
-def request_bytes(P: Problem, max_states: int = 48) -> int:
+def pool_states(P: Problem, max_states: int = 48, pool_cap_bytes: float = 0.0) -> int:
+    """States the request's pool may hold: the whole trajectory when it is
+    short, else the larger of ``max_states`` and what ``pool_cap_bytes``
+    allows (level-1 checkpoints plus recompute slots)."""
+    cap = max(int(max_states), int(pool_cap_bytes // max(state_bytes(P), 1)))
+    return int(min(P.nsteps + 2, max(8, cap)))
+
+
+def request_bytes(P: Problem, max_states: int = 48, pool_cap_bytes: float = 0.0) -> int:
     """Device bytes of one resident request (the admission byte model)."""
     N, M = P.n_nodes, densities(P)
-    pool = pool_states(P, max_states) * M * N * STORAGE[P.precision]
+    pool = pool_states(P, max_states, pool_cap_bytes) * state_bytes(P)
     lam = 2 * M * N * 4
     return int(pool + lam + 8 * N + 5 * N + 16 * 65 * (P.nsteps + 1) + (1 << 20))
 
@@ -97,7 +103,8 @@ def _percentiles(lat):
 
 class Server:
     def __init__(self, reserve_bytes: float = 2 << 30, capacity_bytes: float | None = None,
-                 steps_per_tick: int = 20, max_states: int = 48, stream=None,
+                 steps_per_tick: int = 200, work_per_tick: float = 2e7, max_states: int = 48,
+                 pool_fraction: float = 0.25, stream=None,
                  mem_get_info=None, keep_gradients: bool = True, solver_factory=None,
                  primal_fn=None, adjoint_fn=None):
         # the factories exist so that the scheduling can run against a fake
@@ -111,8 +118,10 @@ class Server:
         info = mem_get_info or torch.cuda.mem_get_info
         free, _ = info()
         self.capacity = float(capacity_bytes) if capacity_bytes is not None else free - reserve_bytes
-        self.steps_per_tick = int(steps_per_tick)
+        self.steps_per_tick = int(steps_per_tick)       # cap of steps per request per tick
+        self.work_per_tick = float(work_per_tick)       # node-steps per request per tick
         self.max_states = int(max_states)
+        self.pool_cap = pool_fraction * self.capacity
         self.keep_gradients = keep_gradients
         self.committed = 0
         self.queue = deque()
@@ -123,7 +132,7 @@ class Server:
 
     # ---- admission ------------------------------------------------------------
     def submit(self, req: Request):
-        req.bytes = request_bytes(req.P, self.max_states)
+        req.bytes = request_bytes(req.P, self.max_states, self.pool_cap)
         self.queue.append(req)
 
     def _admit(self, now: float):
@@ -139,8 +148,7 @@ class Server:
                 break                       # wait for memory to free up (FIFO)
             self.queue.popleft()
             try:
-                budget = pool_states(req.P, self.max_states) * densities(req.P) * \
-                    req.P.n_nodes * STORAGE[req.P.precision]
+                budget = pool_states(req.P, self.max_states, self.pool_cap) * state_bytes(req.P)
                 req.solver = self.solver_factory(req.P, req.theta, stream=self.stream,
                                                  mem_budget=budget)
             except (AlbmError, RuntimeError) as e:
@@ -161,13 +169,15 @@ class Server:
             phase = "primal" if s.time < r.P.nsteps and s.adjoint_time < 0 else "adjoint"
             groups.setdefault((_family(r.P), phase), []).append(r)
         for (fam, phase), rs in groups.items():
-            ss = [r.solver for r in rs]
-            k = self.steps_per_tick
-            if phase == "primal":
-                self.primal_fn(ss, k)
-            else:
-                self.adjoint_fn(ss, k)
-            self.launches += k * ((len(ss) + 63) // 64)
+            # equal node-updates per request per tick: small requests take
+            # many steps while a large one takes few, so they do not wait on it
+            ks = [max(1, min(self.steps_per_tick, int(self.work_per_tick / r.P.n_nodes)))
+                  for r in rs]
+            fn = self.primal_fn if phase == "primal" else self.adjoint_fn
+            for j in range(max(ks)):
+                ss = [r.solver for r, k in zip(rs, ks) if k > j]
+                fn(ss, 1)
+                self.launches += (len(ss) + 63) // 64
 
     def _retire(self, now: float):
         still = []

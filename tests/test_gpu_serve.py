@@ -16,7 +16,7 @@ def test_served_results_equal_alone():
     spec = inputs.serving_requests(12, rate=200.0, seed=7, node_range=(2e3, 2e5), steps=(40, 160))
     reqs = [Request(i, t, P, th) for i, (t, P, th) in enumerate(spec)]
     cap = 6 * max(request_bytes(r.P) for r in reqs)       # forces queueing
-    srv = Server(capacity_bytes=cap, steps_per_tick=16)
+    srv = Server(capacity_bytes=cap, steps_per_tick=16, work_per_tick=2e6)
     stats = srv.run(reqs)
     assert all(r.error is None for r in reqs)
     assert stats.max_resident >= 2

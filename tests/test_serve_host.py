@@ -62,7 +62,7 @@ def _reqs(n, seed=0):
 def test_all_requests_finish_and_results_depend_only_on_the_request():
     reqs = _reqs(12)
     cap = 3.5 * max(request_bytes(r.P) for r in reqs)
-    srv = _server(cap, steps_per_tick=10)
+    srv = _server(cap, steps_per_tick=10, work_per_tick=1e5)
     stats = srv.run(reqs)
     assert all(r.error is None and r.done is not None for r in reqs)
     for r in reqs:
@@ -80,7 +80,7 @@ def test_admission_respects_capacity_and_fifo():
     def watch(srv):
         assert srv.committed <= cap
         seen.append([r.rid for r in srv.active])
-    srv = _server(cap, steps_per_tick=15)
+    srv = _server(cap, steps_per_tick=15, work_per_tick=1e5)
     srv.run(reqs, on_tick=watch)
     order = sorted(reqs, key=lambda r: (r.admitted, r.rid))
     assert [r.rid for r in order] == sorted(r.rid for r in reqs)   # FIFO admission
@@ -94,7 +94,7 @@ def test_oversize_and_malformed_requests_fail_alone():
     big = inputs.exchanger3d(dims=(2048, 1024, 1024), nsteps=10)
     reqs.append(Request(100, reqs[-1].arrival, big, np.zeros(1, np.float32)))
     reqs.append(Request(101, reqs[-1].arrival, reqs[0].P.replace(tau=0.4), reqs[0].theta))
-    srv = _server(cap, steps_per_tick=10)
+    srv = _server(cap, steps_per_tick=10, work_per_tick=1e5)
     srv.run(reqs)
     by = {r.rid: r for r in reqs}
     assert "capacity" in by[100].error
@@ -115,7 +115,7 @@ def test_cancellation_releases_memory():
             assert srv.cancel(victim)
             state["done"] = True
             state["victim"] = victim
-    srv = _server(cap, steps_per_tick=5)
+    srv = _server(cap, steps_per_tick=5, work_per_tick=1e5)
     srv.run(reqs, on_tick=cancel_one)
     v = state["victim"]
     for r in reqs:
