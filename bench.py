@@ -50,12 +50,26 @@ def bytes_per_node(M: int, storage: int, kind: str) -> int:
 
 
 def workload(args) -> inputs.Problem:
-    P = inputs.mixer3d()
+    P = inputs.exchanger3d() if args.workload == "exchanger3d" else inputs.mixer3d()
     if args.nsteps:
         P = P.replace(nsteps=args.nsteps, obj_window=min(P.obj_window, args.nsteps))
     if args.precision != "fp32":
         P = P.replace(precision=args.precision)
     return P
+
+
+def aggregate_ranks(ms_local: float, updates_per_step: float, steps: int, world: int,
+                    device: str = "cuda"):
+    """Whole-job figure of a replicas run: the slowest rank's time bounds the
+    job, and every rank processed ``updates_per_step`` node updates per step
+    (weak scaling).  Returns (max ms over ranks, MLUPS of all ranks)."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * updates_per_step * steps / (ms_max / 1e3) / 1e6
 
 
 def _peaks():
@@ -173,7 +187,7 @@ def run_reference(args):
 
 
 def _config(P, args):
-    return {"workload": "mixer3d", "lattice": P.lattice, "collision": P.collision,
+    return {"workload": args.workload, "lattice": P.lattice, "collision": P.collision,
             "dims": list(P.dims), "nscalars": P.nscalars, "tau": P.tau,
             "primal_steps": P.nsteps, "adjoint_steps": P.nsteps, "ckpt_every": P.ckpt_every,
             "objective": P.objective, "obj_window": P.obj_window, "precision": P.precision,
@@ -195,7 +209,8 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl")
     P = workload(args)
-    theta = inputs.theta_uniform(P, rank)
+    theta = inputs.theta_grf(P, rank) if args.workload == "exchanger3d" else \
+        inputs.theta_uniform(P, rank)
     stream = torch.cuda.Stream()
     th_dev = torch.from_numpy(theta.reshape(-1)).cuda()
     s = Solver(P, th_dev, stream=stream, mem_budget=args.mem_budget)
@@ -229,12 +244,8 @@ def run_ours(args):
     clk = clocks.stop()
     J = s.objective()
     recompute = s.recompute_steps()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
     updates_per_step = N * P.nsteps * 2
-    value = world * updates_per_step * args.steps / (ms_max / 1e3) / 1e6
+    ms_max, value = aggregate_ranks(ms, updates_per_step, args.steps, world)
 
     # kernel-level numbers from the live event record
     n_p, ms_p = prof["primal"]
@@ -413,7 +424,8 @@ def main(argv=None):
     ap.add_argument("--mem-budget", type=float, default=0.0)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="mixer3d", choices=["mixer3d", "batch64", "serve"])
+    ap.add_argument("--workload", default="mixer3d",
+                    choices=["mixer3d", "exchanger3d", "batch64", "serve"])
     ap.add_argument("--count", type=int, default=0, help="instances (batch64) or requests (serve)")
     ap.add_argument("--size-scale", type=float, default=1.0, help="batch64: linear size factor")
     ap.add_argument("--rates", default="2,20,200", help="serve: arrival rates per second")
