@@ -55,6 +55,8 @@ def workload(args) -> inputs.Problem:
         P = P.replace(nsteps=args.nsteps, obj_window=min(P.obj_window, args.nsteps))
     if args.precision != "fp32":
         P = P.replace(precision=args.precision)
+    if args.kernel != "auto":
+        P = P.replace(kernel=args.kernel)
     return P
 
 
@@ -191,6 +193,7 @@ def _config(P, args):
             "dims": list(P.dims), "nscalars": P.nscalars, "tau": P.tau,
             "primal_steps": P.nsteps, "adjoint_steps": P.nsteps, "ckpt_every": P.ckpt_every,
             "objective": P.objective, "obj_window": P.obj_window, "precision": P.precision,
+            "kernel": P.kernel,
             "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -402,7 +405,7 @@ def run_profile_case(args):
     import torch
     from paper_1501_04741_gb300.albm import Solver
     P = inputs.scaled(inputs.mixer3d(), (256, 128, 64), nsteps=4, obj_window=4, ckpt_every=1,
-                      precision=args.precision)
+                      precision=args.precision, kernel=args.kernel)
     th = torch.from_numpy(inputs.theta_uniform(P, 0).reshape(-1)).cuda()
     with Solver(P, th) as s:
         s.primal_step(P.nsteps)
@@ -422,6 +425,8 @@ def main(argv=None):
     ap.add_argument("--nsteps", type=int, default=0, help="override the 10000-step horizon")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--mem-budget", type=float, default=0.0)
+    ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tiles"],
+                    help="step kernels: tile-staged when nx allows (auto), per node, or staged")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="mixer3d",

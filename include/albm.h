@@ -105,6 +105,10 @@ typedef struct {
   int precision;        /* lbm_precision of the stored populations           */
   int ckpt_every;       /* level-1 checkpoint stride (0 = automatic)         */
   double mem_budget;    /* bytes for stored states (0 = automatic)           */
+  int kernel;           /* 0: automatic; 1: one thread per node, gathers from
+                           global memory; 2: tile-staged (TMA bulk copies of
+                           x-row segments into shared memory; needs nx a
+                           multiple of 128)                                  */
 } lbm_params;
 
 /* Create a solver.  Defines the lattice, node types, collision (Sec. 3,

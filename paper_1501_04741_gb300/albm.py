@@ -24,6 +24,7 @@ COLLISION = {"BGK": 0, "MRT": 1}
 PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2}
 POROSITY = {"linear": 0, "power": 1, "ramp": 2}
 OBJECTIVE = {"none": 0, "dissipation": 1, "variance": 2, "heatflux_dp": 3, "mixflux": 4}
+KERNEL = {"auto": 0, "plain": 1, "tiles": 2}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
           4: "LBM_ERR_NONFINITE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 
@@ -48,7 +49,7 @@ class LbmParams(C.Structure):
         ("hot", C.c_int * 4), ("T_hot", C.c_double), ("porosity", C.c_int),
         ("porosity_q", C.c_double), ("objective", C.c_int), ("obj_window", C.c_int),
         ("nsteps", C.c_int), ("precision", C.c_int), ("ckpt_every", C.c_int),
-        ("mem_budget", C.c_double),
+        ("mem_budget", C.c_double), ("kernel", C.c_int),
     ]
 
 
@@ -134,6 +135,7 @@ def make_params(P: Problem, mem_budget: float = 0.0) -> LbmParams:
     p.precision = PRECISION[P.precision]
     p.ckpt_every = int(P.ckpt_every)
     p.mem_budget = float(mem_budget)
+    p.kernel = KERNEL[P.kernel]
     return p
 
 

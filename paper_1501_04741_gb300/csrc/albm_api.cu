@@ -45,8 +45,11 @@ struct lbm_ctx {
   float* theta = nullptr;
   double* grad = nullptr;
   double* stats = nullptr;          // 2 doubles per step 0..nsteps
-  double* partials = nullptr;       // 2 doubles per block of one launch
-  long long nblocks = 0;
+  double* partials = nullptr;       // 2 doubles per block (or tile) of one launch
+  long long nblocks = 0;            // blocks of the one-thread-per-node kernels
+  long long ntiles = 0;             // tiles of the staged kernels
+  bool tiles = false;               // staged kernels in use
+  int* d_err = nullptr;             // bounded-wait failure flag of staged kernels
   unsigned long long* counter = nullptr;
   float* lam[2] = {nullptr, nullptr};
   int lam_cur = 0;
@@ -238,9 +241,21 @@ __global__ void __launch_bounds__(256) fold_partials_kernel(const double* __rest
 }
 }  // namespace albm
 
+// after a synchronisation: report an expired bounded wait of a staged kernel
+static lbm_status check_timeout(lbm_ctx* h) {
+  if (!h->d_err) return LBM_OK;
+  int v = 0;
+  CK(h, cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) {
+    cudaMemset(h->d_err, 0, sizeof(int));
+    FAIL(h, LBM_ERR_TIMEOUT, "a staged kernel's bounded wait for its shared-memory copies expired");
+  }
+  return LBM_OK;
+}
+
 // fold the per-block partials of step t into the objective record
-static lbm_status fold_objective(lbm_ctx* h, int t) {
-  albm::fold_partials_kernel<<<1, 256, 0, h->stream>>>(h->partials, h->nblocks,
+static lbm_status fold_objective(lbm_ctx* h, int t, long long count) {
+  albm::fold_partials_kernel<<<1, 256, 0, h->stream>>>(h->partials, count,
                                                         h->stats + 2 * (size_t)t);
   h->launches_other++;
   cudaError_t e = cudaGetLastError();
@@ -254,12 +269,14 @@ static lbm_status launch_primal(lbm_ctx* h, int src, int dst, int t, bool record
   a.Bin = h->bufs[src];
   a.Bout = h->bufs[dst];
   a.obj = (record && t <= h->p.nsteps && h->c[t] != 0.0) ? h->partials : nullptr;
+  a.err = h->d_err;
   int slot;
   prof_begin(h, kind, &slot);
-  cudaError_t e = h->ks.primal(h->kp, a, h->stream);
+  cudaError_t e = h->tiles ? h->ks.primal_tiles(h->kp, a, h->stream)
+                           : h->ks.primal(h->kp, a, h->stream);
   prof_end(h, slot);
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "primal kernel launch: %s", cudaGetErrorString(e));
-  if (a.obj) return fold_objective(h, t);
+  if (a.obj) return fold_objective(h, t, h->tiles ? h->ntiles : h->nblocks);
   return LBM_OK;
 }
 
@@ -272,7 +289,7 @@ static lbm_status record_final_objective(lbm_ctx* h) {
   cudaError_t e = h->ks.objective(h->kp, a, h->stream);
   h->launches_other++;
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "objective kernel launch: %s", cudaGetErrorString(e));
-  return fold_objective(h, t);
+  return fold_objective(h, t, h->nblocks);
 }
 
 // make f^n available in the pool (recompute from the latest kept state < n)
@@ -345,9 +362,11 @@ static lbm_status launch_adjoint(lbm_ctx* h, int n, int has_next) {
   a.stat_n = (h->p.objective == LBM_OBJ_VARIANCE && h->c[n] != 0.0) ? h->stats + 2 * (size_t)n
                                                                      : nullptr;
   a.has_next = has_next;
+  a.err = h->d_err;
   int slot;
   prof_begin(h, K_ADJOINT, &slot);
-  cudaError_t e = h->ks.adjoint(h->kp, a, h->stream);
+  cudaError_t e = h->tiles ? h->ks.adjoint_tiles(h->kp, a, h->stream)
+                           : h->ks.adjoint(h->kp, a, h->stream);
   prof_end(h, slot);
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "adjoint kernel launch: %s", cudaGetErrorString(e));
   h->lam_cur = 1 - h->lam_cur;
@@ -486,7 +505,22 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   CKC(cudaMalloc(&h->grad, sizeof(double) * (size_t)h->N));
   CKC(cudaMalloc(&h->stats, sizeof(double) * 2 * (size_t)(p.nsteps + 1)));
   h->nblocks = (h->N + albm::kBlock - 1) / albm::kBlock;
-  CKC(cudaMalloc(&h->partials, sizeof(double) * 2 * (size_t)h->nblocks));
+  h->ntiles = h->N / albm::kTile;
+  {
+    const bool eligible = p.nx % albm::kTile == 0;
+    if (p.kernel == 2 && !eligible) {
+      h->err = "tile-staged kernels need nx to be a multiple of 128";
+      return fail(LBM_ERR_ARG);
+    }
+    if (p.kernel < 0 || p.kernel > 2) {
+      h->err = "kernel must be 0 (automatic), 1 (per node) or 2 (tile-staged)";
+      return fail(LBM_ERR_ARG);
+    }
+    h->tiles = (p.kernel == 2) || (p.kernel == 0 && eligible);
+  }
+  CKC(cudaMalloc(&h->partials, sizeof(double) * 2 * (size_t)std::max(h->nblocks, h->ntiles)));
+  CKC(cudaMalloc(&h->d_err, sizeof(int)));
+  CKC(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   CKC(cudaMalloc(&h->counter, sizeof(unsigned long long)));
   CKC(cudaMalloc(&h->lam[0], sizeof(float) * (size_t)h->M * (size_t)h->N));
   CKC(cudaMalloc(&h->lam[1], sizeof(float) * (size_t)h->M * (size_t)h->N));
@@ -545,6 +579,7 @@ void lbm_destroy(lbm_handle h) {
   cudaFree(h->grad);
   cudaFree(h->stats);
   cudaFree(h->partials);
+  cudaFree(h->d_err);
   cudaFree(h->counter);
   cudaFree(h->lam[0]);
   cudaFree(h->lam[1]);
@@ -604,6 +639,10 @@ lbm_status lbm_objective(lbm_handle h, double* J) {
   CK(h, cudaMemcpyAsync(st.data(), h->stats, sizeof(double) * st.size(), cudaMemcpyDeviceToHost,
                         h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  {
+    lbm_status ts = check_timeout(h);
+    if (ts) return ts;
+  }
   double acc = 0.0;
   const double A = h->n_out > 0 ? (double)h->n_out : 1.0;
   for (int n = 0; n <= std::min(h->t, h->p.nsteps); ++n) {
@@ -775,7 +814,7 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
     for (auto& m : moved) {
       lbm_ctx* h = m.first;
       if (h->c[h->t] != 0.0) {
-        lbm_status s = fold_objective(h, h->t);
+        lbm_status s = fold_objective(h, h->t, h->nblocks);
         if (s) return batch_fail(hs[0], h, s);
       }
       h->buf_time[m.second.second] = h->t + 1;
@@ -860,7 +899,10 @@ lbm_status lbm_gradient(lbm_handle h, double* dst) {
   if (!h || !dst) return LBM_ERR_ARG;
   if (h->t_adj < 0) FAIL(h, LBM_ERR_STATE, "no adjoint has run");
   CK(h, cudaMemcpyAsync(dst, h->grad, sizeof(double) * (size_t)h->N, cudaMemcpyDefault, h->stream));
-  if (!is_device_ptr(dst)) CK(h, cudaStreamSynchronize(h->stream));
+  if (!is_device_ptr(dst)) {
+    CK(h, cudaStreamSynchronize(h->stream));
+    return check_timeout(h);
+  }
   return LBM_OK;
 }
 
@@ -956,6 +998,10 @@ lbm_status lbm_check_finite(lbm_handle h, long long* count) {
   unsigned long long c = 0;
   CK(h, cudaMemcpyAsync(&c, h->counter, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  {
+    lbm_status ts = check_timeout(h);
+    if (ts) return ts;
+  }
   *count = (long long)c;
   if (c) FAIL(h, LBM_ERR_NONFINITE, "%llu non-finite values in the state at time %d", c, h->t);
   return LBM_OK;

@@ -391,6 +391,12 @@ __global__ void nonfinite_kernel(const S* __restrict__ B, long long n, unsigned 
 // ---------------------------------------------------------------------------
 // host-side launchers, one set per (lattice, collision, scalars, storage)
 // ---------------------------------------------------------------------------
+}  // namespace albm
+
+#include "albm_tiles.cuh"
+
+namespace albm {
+
 struct StepArgs {
   const void* Bin;
   void* Bout;
@@ -407,6 +413,7 @@ struct StepArgs {
   float* fout;
   int post;
   unsigned long long* count;
+  int* err;             // set by a staged kernel whose bounded wait expired
 };
 
 struct KernelSet {
@@ -418,8 +425,26 @@ struct KernelSet {
   cudaError_t (*nonfinite)(const KParams&, const StepArgs&, int M, cudaStream_t);
   cudaError_t (*primal_batch)(const BatchArgs&, long long blocks, cudaStream_t);
   cudaError_t (*adjoint_batch)(const BatchArgs&, long long blocks, cudaStream_t);
+  cudaError_t (*primal_tiles)(const KParams&, const StepArgs&, cudaStream_t);
+  cudaError_t (*adjoint_tiles)(const KParams&, const StepArgs&, cudaStream_t);
   int storage_bytes;
 };
+
+// persistent grid of a staged kernel: resident blocks per SM x SMs, at most
+// the number of tiles
+template <class K>
+inline cudaError_t tiles_grid(K kernel, size_t smem, long long ntiles, unsigned* grid) {
+  int dev = 0, sms = 0, bps = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kTile, smem);
+  if (e != cudaSuccess) return e;
+  long long g = (long long)sms * (bps > 0 ? bps : 1);
+  *grid = (unsigned)(g < ntiles ? g : ntiles);
+  return cudaSuccess;
+}
 
 constexpr int kBlock = 256;
 
@@ -462,9 +487,41 @@ struct Launch {
     adjoint_batch_kernel<L, NS, MRT, S><<<(unsigned)blocks, kBlock, 0, st>>>(a);
     return cudaGetLastError();
   }
+  static cudaError_t primal_tiles(const KParams& P, const StepArgs& a, cudaStream_t st) {
+    using Lay = TileLayout<L, NS, S, kTile>;
+    const size_t smem = Lay::header + 2 * Lay::primal_stage;
+    auto k = primal_tiles_kernel<L, NS, MRT, S, kTile>;
+    static unsigned grid_cache = 0;
+    static long long tiles_cache = -1;
+    const long long ntiles = P.N / kTile;
+    if (tiles_cache != ntiles) {
+      cudaError_t e = tiles_grid(k, smem, ntiles, &grid_cache);
+      if (e != cudaSuccess) return e;
+      tiles_cache = ntiles;
+    }
+    k<<<grid_cache, kTile, smem, st>>>(P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags, a.obj, a.err);
+    return cudaGetLastError();
+  }
+  static cudaError_t adjoint_tiles(const KParams& P, const StepArgs& a, cudaStream_t st) {
+    using Lay = TileLayout<L, NS, S, kTile>;
+    const size_t smem = Lay::header + 2 * Lay::adjoint_stage;
+    auto k = adjoint_tiles_kernel<L, NS, MRT, S, kTile>;
+    static unsigned grid_cache = 0;
+    static long long tiles_cache = -1;
+    const long long ntiles = P.N / kTile;
+    if (tiles_cache != ntiles) {
+      cudaError_t e = tiles_grid(k, smem, ntiles, &grid_cache);
+      if (e != cudaSuccess) return e;
+      tiles_cache = ntiles;
+    }
+    k<<<grid_cache, kTile, smem, st>>>(P, a.lam_in, (const S*)a.Bin, a.lam_out, a.theta, a.flags,
+                                       a.grad, a.ws, a.stat_n, a.has_next, a.err);
+    return cudaGetLastError();
+  }
   static KernelSet set() {
     return KernelSet{&primal, &objective, &adjoint, &exportf, &importf, &nonfinite,
-                     &primal_batch, &adjoint_batch, (int)sizeof(S)};
+                     &primal_batch, &adjoint_batch, &primal_tiles, &adjoint_tiles,
+                     (int)sizeof(S)};
   }
 };
 

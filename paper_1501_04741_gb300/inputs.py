@@ -58,6 +58,7 @@ class Problem:
     design: tuple = (48, 80, 16, 48, 0, 1)   # (x0, x1, y0, y1, z0, z1) design box
     precision: str = "fp32"          # population storage on the GPU: fp32 | bf16 | fp16
     ckpt_every: int = 0              # level-1 checkpoint stride of the adjoint schedule
+    kernel: str = "auto"             # GPU step kernels: auto | plain | tiles (staged rows)
 
     @property
     def n_nodes(self) -> int:
