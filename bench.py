@@ -425,7 +425,7 @@ def main(argv=None):
     ap.add_argument("--nsteps", type=int, default=0, help="override the 10000-step horizon")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--mem-budget", type=float, default=0.0)
-    ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tiles"],
+    ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tiles", "async"],
                     help="step kernels: tile-staged when nx allows (auto), per node, or staged")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")

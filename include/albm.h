@@ -105,10 +105,12 @@ typedef struct {
   int precision;        /* lbm_precision of the stored populations           */
   int ckpt_every;       /* level-1 checkpoint stride (0 = automatic)         */
   double mem_budget;    /* bytes for stored states (0 = automatic)           */
-  int kernel;           /* 0: automatic; 1: one thread per node, gathers from
-                           global memory; 2: tile-staged (TMA bulk copies of
-                           x-row segments into shared memory; needs nx a
-                           multiple of 128)                                  */
+  int kernel;           /* 0: automatic (one thread per node); 1: one thread
+                           per node, gathers from global memory; 2 or 3:
+                           tile-staged, x-row segments of 128-node tiles
+                           copied to shared memory by TMA bulk copies (2)
+                           or by per-thread cp.async (3); nx a multiple of
+                           128                                              */
 } lbm_params;
 
 /* Create a solver.  Defines the lattice, node types, collision (Sec. 3,

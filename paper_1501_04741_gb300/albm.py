@@ -24,7 +24,7 @@ COLLISION = {"BGK": 0, "MRT": 1}
 PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2}
 POROSITY = {"linear": 0, "power": 1, "ramp": 2}
 OBJECTIVE = {"none": 0, "dissipation": 1, "variance": 2, "heatflux_dp": 3, "mixflux": 4}
-KERNEL = {"auto": 0, "plain": 1, "tiles": 2}
+KERNEL = {"auto": 0, "plain": 1, "tiles": 2, "async": 3}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
           4: "LBM_ERR_NONFINITE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 

@@ -48,7 +48,7 @@ struct lbm_ctx {
   double* partials = nullptr;       // 2 doubles per block (or tile) of one launch
   long long nblocks = 0;            // blocks of the one-thread-per-node kernels
   long long ntiles = 0;             // tiles of the staged kernels
-  bool tiles = false;               // staged kernels in use
+  int staged = 0;                   // 0: per-node kernels; 2: TMA-staged; 3: cp.async-staged
   int* d_err = nullptr;             // bounded-wait failure flag of staged kernels
   unsigned long long* counter = nullptr;
   float* lam[2] = {nullptr, nullptr};
@@ -272,11 +272,12 @@ static lbm_status launch_primal(lbm_ctx* h, int src, int dst, int t, bool record
   a.err = h->d_err;
   int slot;
   prof_begin(h, kind, &slot);
-  cudaError_t e = h->tiles ? h->ks.primal_tiles(h->kp, a, h->stream)
-                           : h->ks.primal(h->kp, a, h->stream);
+  cudaError_t e = h->staged == 2   ? h->ks.primal_tiles(h->kp, a, h->stream)
+                  : h->staged == 3 ? h->ks.primal_async(h->kp, a, h->stream)
+                                   : h->ks.primal(h->kp, a, h->stream);
   prof_end(h, slot);
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "primal kernel launch: %s", cudaGetErrorString(e));
-  if (a.obj) return fold_objective(h, t, h->tiles ? h->ntiles : h->nblocks);
+  if (a.obj) return fold_objective(h, t, h->staged ? h->ntiles : h->nblocks);
   return LBM_OK;
 }
 
@@ -365,8 +366,9 @@ static lbm_status launch_adjoint(lbm_ctx* h, int n, int has_next) {
   a.err = h->d_err;
   int slot;
   prof_begin(h, K_ADJOINT, &slot);
-  cudaError_t e = h->tiles ? h->ks.adjoint_tiles(h->kp, a, h->stream)
-                           : h->ks.adjoint(h->kp, a, h->stream);
+  cudaError_t e = h->staged == 2   ? h->ks.adjoint_tiles(h->kp, a, h->stream)
+                  : h->staged == 3 ? h->ks.adjoint_async(h->kp, a, h->stream)
+                                   : h->ks.adjoint(h->kp, a, h->stream);
   prof_end(h, slot);
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "adjoint kernel launch: %s", cudaGetErrorString(e));
   h->lam_cur = 1 - h->lam_cur;
@@ -508,15 +510,15 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   h->ntiles = h->N / albm::kTile;
   {
     const bool eligible = p.nx % albm::kTile == 0;
-    if (p.kernel == 2 && !eligible) {
+    if (p.kernel < 0 || p.kernel > 3) {
+      h->err = "kernel must be 0 (automatic), 1 (per node), 2 or 3 (tile-staged)";
+      return fail(LBM_ERR_ARG);
+    }
+    if (p.kernel >= 2 && !eligible) {
       h->err = "tile-staged kernels need nx to be a multiple of 128";
       return fail(LBM_ERR_ARG);
     }
-    if (p.kernel < 0 || p.kernel > 2) {
-      h->err = "kernel must be 0 (automatic), 1 (per node) or 2 (tile-staged)";
-      return fail(LBM_ERR_ARG);
-    }
-    h->tiles = (p.kernel == 2) || (p.kernel == 0 && eligible);
+    h->staged = p.kernel >= 2 ? p.kernel : 0;
   }
   CKC(cudaMalloc(&h->partials, sizeof(double) * 2 * (size_t)std::max(h->nblocks, h->ntiles)));
   CKC(cudaMalloc(&h->d_err, sizeof(int)));

@@ -427,6 +427,8 @@ struct KernelSet {
   cudaError_t (*adjoint_batch)(const BatchArgs&, long long blocks, cudaStream_t);
   cudaError_t (*primal_tiles)(const KParams&, const StepArgs&, cudaStream_t);
   cudaError_t (*adjoint_tiles)(const KParams&, const StepArgs&, cudaStream_t);
+  cudaError_t (*primal_async)(const KParams&, const StepArgs&, cudaStream_t);
+  cudaError_t (*adjoint_async)(const KParams&, const StepArgs&, cudaStream_t);
   int storage_bytes;
 };
 
@@ -518,10 +520,41 @@ struct Launch {
                                        a.grad, a.ws, a.stat_n, a.has_next, a.err);
     return cudaGetLastError();
   }
+  static cudaError_t primal_async(const KParams& P, const StepArgs& a, cudaStream_t st) {
+    using Lay = TileLayout<L, NS, S, kTile>;
+    const size_t smem = Lay::header_async + 2 * Lay::primal_stage;
+    auto k = primal_async_kernel<L, NS, MRT, S, kTile>;
+    static unsigned grid_cache = 0;
+    static long long tiles_cache = -1;
+    const long long ntiles = P.N / kTile;
+    if (tiles_cache != ntiles) {
+      cudaError_t e = tiles_grid(k, smem, ntiles, &grid_cache);
+      if (e != cudaSuccess) return e;
+      tiles_cache = ntiles;
+    }
+    k<<<grid_cache, kTile, smem, st>>>(P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags, a.obj);
+    return cudaGetLastError();
+  }
+  static cudaError_t adjoint_async(const KParams& P, const StepArgs& a, cudaStream_t st) {
+    using Lay = TileLayout<L, NS, S, kTile>;
+    const size_t smem = Lay::header_async + 2 * Lay::adjoint_stage;
+    auto k = adjoint_async_kernel<L, NS, MRT, S, kTile>;
+    static unsigned grid_cache = 0;
+    static long long tiles_cache = -1;
+    const long long ntiles = P.N / kTile;
+    if (tiles_cache != ntiles) {
+      cudaError_t e = tiles_grid(k, smem, ntiles, &grid_cache);
+      if (e != cudaSuccess) return e;
+      tiles_cache = ntiles;
+    }
+    k<<<grid_cache, kTile, smem, st>>>(P, a.lam_in, (const S*)a.Bin, a.lam_out, a.theta, a.flags,
+                                       a.grad, a.ws, a.stat_n, a.has_next);
+    return cudaGetLastError();
+  }
   static KernelSet set() {
     return KernelSet{&primal, &objective, &adjoint, &exportf, &importf, &nonfinite,
                      &primal_batch, &adjoint_batch, &primal_tiles, &adjoint_tiles,
-                     (int)sizeof(S)};
+                     &primal_async, &adjoint_async, (int)sizeof(S)};
   }
 };
 

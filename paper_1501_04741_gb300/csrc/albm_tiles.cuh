@@ -116,6 +116,7 @@ struct TileLayout {
   static constexpr size_t primal_stage = (size_t)M * W * sizeof(S);
   static constexpr size_t adjoint_stage = (size_t)M * W * sizeof(S) + (size_t)M * WL * sizeof(float);
   static constexpr size_t header = 128;             // two mbarriers, padded
+  static constexpr size_t header_async = ((4 * M * 8 + 127) / 128) * 128;  // row bases
 };
 
 template <class L, int NS, bool MRT, class S, int TX>
@@ -263,6 +264,234 @@ __global__ void __launch_bounds__(TX) adjoint_tiles_kernel(
       return;
     }
     phase[sg] ^= 1u;
+    const long long row = t / tiles_x;
+    const int x0 = (int)(t - row * tiles_x) * TX;
+    const int y = (int)(row % P.ny);
+    const int lx = threadIdx.x;
+    const long long idx = row * Lx + x0 + lx;
+    const S* fs = reinterpret_cast<const S*>(base[sg]);
+    const float* ls = reinterpret_cast<const float*>(base[sg] + (size_t)M * W * sizeof(S));
+    float d[Q], g[NSA][QS];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = to_f(fs[i * W + H + lx - L::ex(i)]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < QS; ++i) g[s][i] = to_f(fs[(Q + s * QS + i) * W + H + lx - LS::ex(i)]);
+    const uint8_t type = flags[idx];
+    const float cbar = stat_n != nullptr ? (float)(stat_n[0] * (double)P.inv_A_out) : 0.0f;
+    auto load = [&](float* a, float (*b)[QS]) {
+      if (has_next) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) a[i] = ls[i * WL + HL + lx + L::ex(i)];
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+          for (int i = 0; i < QS; ++i) b[s][i] = ls[(Q + s * QS + i) * WL + HL + lx + LS::ex(i)];
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) a[i] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < NSA; ++s)
+#pragma unroll
+          for (int i = 0; i < QS; ++i) b[s][i] = 0.0f;
+      }
+    };
+    float lam[Q], lamg[NSA][QS], dth;
+    Ops::reverse(P, type, theta[idx], y, d, g, load, ws, cbar, lam, lamg, dth);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st(lam_out + (long long)i * P.N + idx, lam[i]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < QS; ++i) st(lam_out + (long long)(Q + s * QS + i) * P.N + idx, lamg[s][i]);
+    if (type == FLUID || type == INLET || type == OUTLET) grad[idx] += (double)dth;
+    __syncthreads();  // the stage may be refilled from here on
+  }
+}
+
+}  // namespace albm
+
+// ---------------------------------------------------------------------------
+// Variant staged with cp.async (16-byte copies issued by every thread of the
+// block, completion tracked by commit/wait groups, no mbarrier waits).  The
+// staged row segment and its halos are the same as above; each 16-byte
+// chunk k of the segment [x0 - H, x0 + TX + H) of density m is one copy, the
+// first and last chunk wrapping to the other end of the row when the tile
+// touches it.
+// ---------------------------------------------------------------------------
+namespace albm {
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Issue the chunks of rows [0, nrows) of one stage: row r holds density
+// row_m[r] from source row base row_base[r] (element offsets, wrap applied
+// for y and z); every row is W = TX + 2H elements = TX/H + 2 chunks.
+template <class T, int TX>
+__device__ __forceinline__ void async_rows(T* dst, const T* src_base, const long long* row_base,
+                                           int nrows, int x0, int Lx) {
+  constexpr int H = 16 / (int)sizeof(T);
+  constexpr int CH = TX / H + 2;  // chunks per row
+  constexpr int W = TX + 2 * H;
+  for (int c = threadIdx.x; c < nrows * CH; c += blockDim.x) {
+    const int r = c / CH, k = c - r * CH;
+    int xs = x0 - H + k * H;  // first element of the chunk
+    if (xs < 0) xs += Lx;
+    if (xs >= Lx) xs -= Lx;
+    cp_async16(dst + r * W + k * H, src_base + row_base[r] + xs);
+  }
+}
+
+template <class L, int NS, bool MRT, class S, int TX>
+__global__ void __launch_bounds__(TX) primal_async_kernel(KParams P, const S* __restrict__ Bin,
+                                                          S* __restrict__ Bout,
+                                                          const float* __restrict__ theta,
+                                                          const uint8_t* __restrict__ flags,
+                                                          double* __restrict__ obj) {
+  using Ops = NodeOps<L, NS, MRT>;
+  using LS = typename Ops::LS;
+  using Lay = TileLayout<L, NS, S, TX>;
+  constexpr int Q = Ops::Q, QS = Ops::QS, NSA = Ops::NSA, M = Lay::M, H = Lay::H, W = Lay::W;
+  extern __shared__ __align__(128) unsigned char smem[];
+  long long* rbase = reinterpret_cast<long long*>(smem);                 // 2 x M row bases
+  S* stage[2] = {reinterpret_cast<S*>(smem + Lay::header_async),
+                 reinterpret_cast<S*>(smem + Lay::header_async + Lay::primal_stage)};
+  const int Lx = P.nx;
+  const int tiles_x = Lx / TX;
+  const long long ntiles = (long long)tiles_x * P.ny * P.nz;
+  auto bases = [&](long long t, int sg) {  // source row of every density
+    const long long row = t / tiles_x;
+    const int y = (int)(row % P.ny), z = (int)(row / P.ny);
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+      int ey = 0, ez = 0;
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+        if (i == m) {
+          ey = i < Q ? L::ey(i) : LS::ey((i - Q) % QS);
+          ez = i < Q ? L::ez(i) : LS::ez((i - Q) % QS);
+        }
+      const int ys = wrap(y - ey, P.ny), zs = wrap(z - ez, P.nz);
+      rbase[sg * M + m] = (long long)m * P.N + ((long long)zs * P.ny + ys) * Lx;
+    }
+  };
+  auto issue = [&](long long t, int sg) {
+    const long long row = t / tiles_x;
+    const int x0 = (int)(t - row * tiles_x) * TX;
+    async_rows<S, TX>(stage[sg], Bin, rbase + sg * M, M, x0, Lx);
+    cp_async_commit();
+  };
+  long long t = blockIdx.x;
+  if (t < ntiles) {
+    bases(t, 0);
+    __syncthreads();
+    issue(t, 0);
+  }
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int sg = it & 1;
+    const long long tn = t + gridDim.x;
+    if (tn < ntiles) {
+      bases(tn, sg ^ 1);
+      __syncthreads();
+      issue(tn, sg ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const long long row = t / tiles_x;
+    const int x0 = (int)(t - row * tiles_x) * TX;
+    const int y = (int)(row % P.ny);
+    const int lx = threadIdx.x;
+    const long long idx = row * Lx + x0 + lx;
+    const S* sb = stage[sg];
+    float d[Q], g[NSA][QS];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = to_f(sb[i * W + H + lx - L::ex(i)]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < QS; ++i) g[s][i] = to_f(sb[(Q + s * QS + i) * W + H + lx - LS::ex(i)]);
+    double o1 = 0.0, o2 = 0.0;
+    Ops::forward(P, flags[idx], theta[idx], y, d, g, obj != nullptr, o1, o2);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, d[i]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < QS; ++i) st(Bout + (long long)(Q + s * QS + i) * P.N + idx, g[s][i]);
+    if (obj != nullptr) block_partial2(o1, o2, obj + 2 * t);
+    __syncthreads();  // the stage may be refilled from here on
+  }
+}
+
+template <class L, int NS, bool MRT, class S, int TX>
+__global__ void __launch_bounds__(TX) adjoint_async_kernel(
+    KParams P, const float* __restrict__ lam_in, const S* __restrict__ Bn,
+    float* __restrict__ lam_out, const float* __restrict__ theta, const uint8_t* __restrict__ flags,
+    double* __restrict__ grad, float ws, const double* __restrict__ stat_n, int has_next) {
+  using Ops = NodeOps<L, NS, MRT>;
+  using LS = typename Ops::LS;
+  using Lay = TileLayout<L, NS, S, TX>;
+  constexpr int Q = Ops::Q, QS = Ops::QS, NSA = Ops::NSA, M = Lay::M, H = Lay::H, W = Lay::W;
+  constexpr int HL = Lay::HL, WL = Lay::WL;
+  extern __shared__ __align__(128) unsigned char smem[];
+  long long* rbase = reinterpret_cast<long long*>(smem);  // 2 stages x (M f-rows + M lambda-rows)
+  unsigned char* base[2] = {smem + Lay::header_async, smem + Lay::header_async + Lay::adjoint_stage};
+  const int Lx = P.nx;
+  const int tiles_x = Lx / TX;
+  const long long ntiles = (long long)tiles_x * P.ny * P.nz;
+  auto bases = [&](long long t, int sg) {
+    const long long row = t / tiles_x;
+    const int y = (int)(row % P.ny), z = (int)(row / P.ny);
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+      int ey = 0, ez = 0;
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+        if (i == m) {
+          ey = i < Q ? L::ey(i) : LS::ey((i - Q) % QS);
+          ez = i < Q ? L::ez(i) : LS::ez((i - Q) % QS);
+        }
+      rbase[sg * 2 * M + m] =
+          (long long)m * P.N + ((long long)wrap(z - ez, P.nz) * P.ny + wrap(y - ey, P.ny)) * Lx;
+      rbase[sg * 2 * M + M + m] =
+          (long long)m * P.N + ((long long)wrap(z + ez, P.nz) * P.ny + wrap(y + ey, P.ny)) * Lx;
+    }
+  };
+  auto issue = [&](long long t, int sg) {
+    const long long row = t / tiles_x;
+    const int x0 = (int)(t - row * tiles_x) * TX;
+    S* fs = reinterpret_cast<S*>(base[sg]);
+    float* ls = reinterpret_cast<float*>(base[sg] + (size_t)M * W * sizeof(S));
+    async_rows<S, TX>(fs, Bn, rbase + sg * 2 * M, M, x0, Lx);
+    if (has_next) async_rows<float, TX>(ls, lam_in, rbase + sg * 2 * M + M, M, x0, Lx);
+    cp_async_commit();
+  };
+  long long t = blockIdx.x;
+  if (t < ntiles) {
+    bases(t, 0);
+    __syncthreads();
+    issue(t, 0);
+  }
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int sg = it & 1;
+    const long long tn = t + gridDim.x;
+    if (tn < ntiles) {
+      bases(tn, sg ^ 1);
+      __syncthreads();
+      issue(tn, sg ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
     const long long row = t / tiles_x;
     const int x0 = (int)(t - row * tiles_x) * TX;
     const int y = (int)(row % P.ny);

@@ -55,9 +55,10 @@ def _random_state(o, seed):
     return F.to(torch.float32).to(torch.float64)
 
 
+@pytest.mark.parametrize("kernel", ["tiles", "async"])
 @pytest.mark.parametrize("name", [n for n in CASES if not n.endswith("bf16")])
-def test_tiles_one_step_against_oracle(name):
-    P = CASES[name].replace(objective="none", obj_window=0, kernel="tiles")
+def test_tiles_one_step_against_oracle(name, kernel):
+    P = CASES[name].replace(objective="none", obj_window=0, kernel=kernel)
     th = _theta(P, 1)
     o = Oracle(P, th)
     F = _random_state(o, 2)
@@ -89,17 +90,19 @@ def test_tiles_match_per_node_kernels(name):
     P = CASES[name]
     th = _theta(P, 3)
     out = {}
-    for kern in ("plain", "tiles"):
+    for kern in ("plain", "tiles", "async"):
         with _solver(P.replace(kernel=kern), th) as s:
             s.primal_step(P.nsteps)
             f = _np(s.populations(0))
             J = s.objective()
             s.adjoint_step(P.nsteps)
             out[kern] = (f, J, _np(s.gradient()))
-    (f0, J0, g0), (f1, J1, g1) = out["plain"], out["tiles"]
-    assert np.abs(f1 - f0).max() <= 1e-6 * np.abs(f0).max()
-    assert abs(J1 - J0) <= 1e-6 * abs(J0)
-    assert np.abs(g1 - g0).max() <= 1e-5 * np.abs(g0).max()
+    f0, J0, g0 = out["plain"]
+    for kern in ("tiles", "async"):
+        f1, J1, g1 = out[kern]
+        assert np.abs(f1 - f0).max() <= 1e-6 * np.abs(f0).max()
+        assert abs(J1 - J0) <= 1e-6 * abs(J0)
+        assert np.abs(g1 - g0).max() <= 1e-5 * np.abs(g0).max()
 
 
 def test_tiles_refused_when_nx_is_not_a_tile_multiple():
