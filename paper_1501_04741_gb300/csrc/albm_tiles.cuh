@@ -117,6 +117,8 @@ struct TileLayout {
   static constexpr size_t adjoint_stage = (size_t)M * W * sizeof(S) + (size_t)M * WL * sizeof(float);
   static constexpr size_t header = 128;             // two mbarriers, padded
   static constexpr size_t header_async = ((4 * M * 8 + 127) / 128) * 128;  // row bases
+  // one issuing thread per staged row (f and lambda rows of the adjoint)
+  static_assert(2 * M <= TX, "a tile needs a thread per staged row");
 };
 
 template <class L, int NS, bool MRT, class S, int TX>
@@ -143,16 +145,22 @@ __global__ void __launch_bounds__(TX) primal_tiles_kernel(KParams P, const S* __
     mbar_fence_init();
   }
   __syncthreads();
+  // thread 0 registers the stage's bytes once; thread m < M issues the
+  // copies of density m (transient negative transaction counts are allowed)
   auto issue = [&](long long t, int sg) {
-    if (threadIdx.x != 0) return;
     const long long row = t / tiles_x;
     const int x0 = (int)(t - row * tiles_x) * TX;
     const int y = (int)(row % P.ny), z = (int)(row / P.ny);
-    mbar_arrive_expect_tx(&bar[sg], (uint32_t)Lay::primal_stage);
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar[sg], (uint32_t)Lay::primal_stage);
+    const int m = threadIdx.x;
+    if (m < M) {
+      int ey = 0, ez = 0;
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      const int ey = m < Q ? L::ey(m) : LS::ey((m - Q) % QS);
-      const int ez = m < Q ? L::ez(m) : LS::ez((m - Q) % QS);
+      for (int i = 0; i < M; ++i)
+        if (i == m) {
+          ey = i < Q ? L::ey(i) : LS::ey((i - Q) % QS);
+          ez = i < Q ? L::ez(i) : LS::ez((i - Q) % QS);
+        }
       const int ys = wrap(y - ey, P.ny), zs = wrap(z - ez, P.nz);
       const S* src = Bin + (long long)m * P.N + ((long long)zs * P.ny + ys) * Lx;
       load_row_segment<S, TX>(stage[sg] + m * W, src, x0, Lx, &bar[sg]);
@@ -226,23 +234,30 @@ __global__ void __launch_bounds__(TX) adjoint_tiles_kernel(
   __syncthreads();
   const uint32_t stage_bytes =
       (uint32_t)((size_t)M * W * sizeof(S) + (has_next ? (size_t)M * WL * sizeof(float) : 0));
+  // thread 0 registers the stage's bytes once; thread m < M issues the f
+  // copies of density m and thread M + m its lambda copies
   auto issue = [&](long long t, int sg) {
-    if (threadIdx.x != 0) return;
     const long long row = t / tiles_x;
     const int x0 = (int)(t - row * tiles_x) * TX;
     const int y = (int)(row % P.ny), z = (int)(row / P.ny);
     S* fs = reinterpret_cast<S*>(base[sg]);
     float* ls = reinterpret_cast<float*>(base[sg] + (size_t)M * W * sizeof(S));
-    mbar_arrive_expect_tx(&bar[sg], stage_bytes);
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar[sg], stage_bytes);
+    const bool lam_row = threadIdx.x >= M;
+    const int m = lam_row ? threadIdx.x - M : threadIdx.x;
+    if (m < M && (!lam_row || has_next)) {
+      int ey = 0, ez = 0;
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      const int ey = m < Q ? L::ey(m) : LS::ey((m - Q) % QS);
-      const int ez = m < Q ? L::ez(m) : LS::ez((m - Q) % QS);
-      // f^n_m(x) = B_m(x - e_m)
-      const int ys = wrap(y - ey, P.ny), zs = wrap(z - ez, P.nz);
-      load_row_segment<S, TX>(fs + m * W, Bn + (long long)m * P.N + ((long long)zs * P.ny + ys) * Lx,
-                              x0, Lx, &bar[sg]);
-      if (has_next) {  // lambda^{n+1}_m(x + e_m)
+      for (int i = 0; i < M; ++i)
+        if (i == m) {
+          ey = i < Q ? L::ey(i) : LS::ey((i - Q) % QS);
+          ez = i < Q ? L::ez(i) : LS::ez((i - Q) % QS);
+        }
+      if (!lam_row) {  // f^n_m(x) = B_m(x - e_m)
+        const int ys = wrap(y - ey, P.ny), zs = wrap(z - ez, P.nz);
+        load_row_segment<S, TX>(fs + m * W, Bn + (long long)m * P.N + ((long long)zs * P.ny + ys) * Lx,
+                                x0, Lx, &bar[sg]);
+      } else {         // lambda^{n+1}_m(x + e_m)
         const int yl = wrap(y + ey, P.ny), zl = wrap(z + ez, P.nz);
         load_row_segment<float, TX>(ls + m * WL,
                                     lam_in + (long long)m * P.N + ((long long)zl * P.ny + yl) * Lx,
