@@ -180,6 +180,33 @@ static lbm_status acquire(lbm_ctx* h, int* out) {
   return LBM_OK;
 }
 
+// Forward pass: a free buffer, a new one while the pool is below its
+// budget, else the buffer of the oldest kept state that is neither a level-1
+// checkpoint nor `keep`.  The forward pass thus leaves the most recent states
+// in the pool, which the adjoint needs first, instead of recomputing them.
+static lbm_status acquire_evict(lbm_ctx* h, int keep, int* out) {
+  for (size_t i = 0; i < h->bufs.size(); ++i)
+    if (h->buf_time[i] == -1) {
+      *out = (int)i;
+      return LBM_OK;
+    }
+  if ((int)h->bufs.size() < h->max_bufs) return acquire(h, out);
+  int best = -1, best_t = 0;
+  for (size_t i = 0; i < h->bufs.size(); ++i) {
+    const int t = h->buf_time[i];
+    if (t >= 0 && t != keep && t % h->ckpt != 0 && (best < 0 || t < best_t)) {
+      best = (int)i;
+      best_t = t;
+    }
+  }
+  if (best < 0)
+    FAIL(h, LBM_ERR_OOM, "state pool exhausted by checkpoints (%d buffers of %zu bytes)",
+         h->max_bufs, h->state_bytes);
+  h->buf_time[best] = -1;
+  *out = best;
+  return LBM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // profiling events
 // ---------------------------------------------------------------------------
@@ -553,7 +580,7 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   if (budget <= 0) {
     size_t fr = 0, tot = 0;
     CKC(cudaMemGetInfo(&fr, &tot));
-    budget = 0.8 * (double)fr;
+    budget = 0.85 * (double)fr;
   }
   h->max_bufs = (int)std::max(3.0, std::floor(budget / (double)h->state_bytes));
   // level-1 checkpoint stride: given, or every state if all fit, else
@@ -618,12 +645,11 @@ lbm_status lbm_primal_step(lbm_handle h, int k) {
   for (int i = 0; i < k; ++i) {
     const int src = find_buf(h, h->t);
     int dst;
-    lbm_status s = acquire(h, &dst);
+    lbm_status s = acquire_evict(h, h->t, &dst);
     if (s) return s;
     s = launch_primal(h, src, dst, h->t, true, K_PRIMAL);
     if (s) return s;
-    h->buf_time[dst] = h->t + 1;
-    if (h->t % h->ckpt != 0) h->buf_time[src] = -1;  // not a checkpoint
+    h->buf_time[dst] = h->t + 1;  // f^t stays while the pool has room
     h->t += 1;
   }
   if (k > 0 && h->t == h->p.nsteps) {
@@ -789,7 +815,7 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
       if (h->t >= h->p.nsteps) continue;  // horizon reached
       const int src = find_buf(h, h->t);
       int dst;
-      lbm_status s = acquire(h, &dst);
+      lbm_status s = acquire_evict(h, h->t, &dst);
       if (s) return batch_fail(hs[0], h, s);
       h->buf_time[dst] = -2;  // reserved until the launch is issued
       albm::InstanceDesc& D = args.inst[args.n++];
@@ -820,7 +846,6 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
         if (s) return batch_fail(hs[0], h, s);
       }
       h->buf_time[m.second.second] = h->t + 1;
-      if (h->t % h->ckpt != 0) h->buf_time[m.second.first] = -1;
       h->t += 1;
       if (h->t == h->p.nsteps) {
         lbm_status s = record_final_objective(h);
