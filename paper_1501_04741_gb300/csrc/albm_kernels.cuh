@@ -30,6 +30,10 @@ namespace albm {
 #ifndef ALBM_ADJOINT_MINB
 #define ALBM_ADJOINT_MINB 1
 #endif
+// threads per block of the single-instance adjoint kernel
+#ifndef ALBM_ADJ_BLOCK
+#define ALBM_ADJ_BLOCK 256
+#endif
 // streaming (evict-first) stores for the state and adjoint outputs, which
 // the same kernel never reads back
 #ifndef ALBM_STREAM_STORES
@@ -260,7 +264,7 @@ __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __re
 }
 
 template <class L, int NS, bool MRT, class S>
-__global__ void __launch_bounds__(256, ALBM_ADJOINT_MINB) adjoint_kernel(KParams P, const float* __restrict__ lam_in,
+__global__ void __launch_bounds__(ALBM_ADJ_BLOCK, ALBM_ADJOINT_MINB) adjoint_kernel(KParams P, const float* __restrict__ lam_in,
                                                       const S* __restrict__ Bn,
                                                       float* __restrict__ lam_out,
                                                       const float* __restrict__ theta,
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(256, ALBM_PRIMAL_MINB) primal_batch_kernel(con
 }
 
 template <class L, int NS, bool MRT, class S>
-__global__ void __launch_bounds__(256, ALBM_ADJOINT_MINB) adjoint_batch_kernel(const __grid_constant__ BatchArgs args) {
+__global__ void __launch_bounds__(256, 2) adjoint_batch_kernel(const __grid_constant__ BatchArgs args) {
   const InstanceDesc& D = args.inst[batch_instance(args)];
   const long long block = (long long)blockIdx.x - D.block_begin;
   adjoint_body<L, NS, MRT, S>(D.P, D.lam_in, (const S*)D.Bin, D.lam_out, D.theta, D.flags, D.grad,
@@ -464,7 +468,8 @@ struct Launch {
     return cudaGetLastError();
   }
   static cudaError_t adjoint(const KParams& P, const StepArgs& a, cudaStream_t st) {
-    adjoint_kernel<L, NS, MRT, S><<<blocks(P), kBlock, 0, st>>>(
+    const unsigned nb = (unsigned)((P.N + ALBM_ADJ_BLOCK - 1) / ALBM_ADJ_BLOCK);
+    adjoint_kernel<L, NS, MRT, S><<<nb, ALBM_ADJ_BLOCK, 0, st>>>(
         P, a.lam_in, (const S*)a.Bin, a.lam_out, a.theta, a.flags, a.grad, a.ws, a.stat_n,
         a.has_next);
     return cudaGetLastError();
