@@ -304,7 +304,7 @@ static lbm_status launch_primal(lbm_ctx* h, int src, int dst, int t, bool record
                                    : h->ks.primal(h->kp, a, h->stream);
   prof_end(h, slot);
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "primal kernel launch: %s", cudaGetErrorString(e));
-  if (a.obj) return fold_objective(h, t, h->staged ? h->ntiles : h->nblocks);
+  if (a.obj) return fold_objective(h, t, h->staged ? h->ntiles : h->ks.primal_partials(h->kp));
   return LBM_OK;
 }
 
@@ -547,7 +547,9 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
     }
     h->staged = p.kernel >= 2 ? p.kernel : 0;
   }
-  CKC(cudaMalloc(&h->partials, sizeof(double) * 2 * (size_t)std::max(h->nblocks, h->ntiles)));
+  CKC(cudaMalloc(&h->partials, sizeof(double) * 2 *
+                                  (size_t)std::max(std::max(h->nblocks, h->ntiles),
+                                                   h->ks.primal_partials(h->kp))));
   CKC(cudaMalloc(&h->d_err, sizeof(int)));
   CKC(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   CKC(cudaMalloc(&h->counter, sizeof(unsigned long long)));

@@ -27,12 +27,16 @@ namespace albm {
 #ifndef ALBM_PRIMAL_MINB
 #define ALBM_PRIMAL_MINB 4
 #endif
-#ifndef ALBM_ADJOINT_MINB
-#define ALBM_ADJOINT_MINB 1
+#ifndef ALBM_PRIMAL_BLOCK
+#define ALBM_PRIMAL_BLOCK 256
 #endif
-// threads per block of the single-instance adjoint kernel
+#ifndef ALBM_ADJOINT_MINB
+#define ALBM_ADJOINT_MINB 4
+#endif
+// threads per block of the single-instance adjoint kernel (4 blocks of 128
+// per SM at its ~119 registers measured 4 % faster than 2 blocks of 256)
 #ifndef ALBM_ADJ_BLOCK
-#define ALBM_ADJ_BLOCK 256
+#define ALBM_ADJ_BLOCK 128
 #endif
 // streaming (evict-first) stores for the state and adjoint outputs, which
 // the same kernel never reads back
@@ -176,7 +180,7 @@ __device__ __forceinline__ void primal_body(const KParams& P, const S* __restric
 }
 
 template <class L, int NS, bool MRT, class S>
-__global__ void __launch_bounds__(256, ALBM_PRIMAL_MINB) primal_kernel(KParams P, const S* __restrict__ Bin,
+__global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK, ALBM_PRIMAL_MINB) primal_kernel(KParams P, const S* __restrict__ Bin,
                                                      S* __restrict__ Bout,
                                                      const float* __restrict__ theta,
                                                      const uint8_t* __restrict__ flags,
@@ -316,7 +320,7 @@ __device__ __forceinline__ int batch_instance(const BatchArgs& a) {
 }
 
 template <class L, int NS, bool MRT, class S>
-__global__ void __launch_bounds__(256, ALBM_PRIMAL_MINB) primal_batch_kernel(const __grid_constant__ BatchArgs args) {
+__global__ void __launch_bounds__(256, 4) primal_batch_kernel(const __grid_constant__ BatchArgs args) {
   const InstanceDesc& D = args.inst[batch_instance(args)];
   const int block = (int)((long long)blockIdx.x - D.block_begin);
   primal_body<L, NS, MRT, S>(D.P, (const S*)D.Bin, (S*)D.Bout, D.theta, D.flags, D.obj,
@@ -433,6 +437,7 @@ struct KernelSet {
   cudaError_t (*adjoint_tiles)(const KParams&, const StepArgs&, cudaStream_t);
   cudaError_t (*primal_async)(const KParams&, const StepArgs&, cudaStream_t);
   cudaError_t (*adjoint_async)(const KParams&, const StepArgs&, cudaStream_t);
+  long long (*primal_partials)(const KParams&);  // objective slots the primal kernel writes
   int storage_bytes;
 };
 
@@ -458,7 +463,8 @@ template <class L, int NS, bool MRT, class S>
 struct Launch {
   static unsigned blocks(const KParams& P) { return (unsigned)((P.N + kBlock - 1) / kBlock); }
   static cudaError_t primal(const KParams& P, const StepArgs& a, cudaStream_t st) {
-    primal_kernel<L, NS, MRT, S><<<blocks(P), kBlock, 0, st>>>(
+    const unsigned nb = (unsigned)((P.N + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK);
+    primal_kernel<L, NS, MRT, S><<<nb, ALBM_PRIMAL_BLOCK, 0, st>>>(
         P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags, a.obj);
     return cudaGetLastError();
   }
@@ -556,10 +562,13 @@ struct Launch {
                                        a.grad, a.ws, a.stat_n, a.has_next);
     return cudaGetLastError();
   }
+  static long long primal_partials(const KParams& P) {
+    return (P.N + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK;
+  }
   static KernelSet set() {
     return KernelSet{&primal, &objective, &adjoint, &exportf, &importf, &nonfinite,
                      &primal_batch, &adjoint_batch, &primal_tiles, &adjoint_tiles,
-                     &primal_async, &adjoint_async, (int)sizeof(S)};
+                     &primal_async, &adjoint_async, &primal_partials, (int)sizeof(S)};
   }
 };
 
