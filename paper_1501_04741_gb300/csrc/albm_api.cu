@@ -124,19 +124,6 @@ void build_flags(const lbm_params& p, std::vector<uint8_t>& fl) {
       }
 }
 
-template <class L>
-void mrt_rates(const lbm_params& p, float omega, float* r) {
-  for (int k = 0; k < 19; ++k) r[k] = 0.f;
-  for (int k = 0; k < L::NMOM; ++k) {
-    double D = 0.0;
-    for (int i = 0; i < L::Q; ++i) D += double(L::U(k, i)) * double(L::U(k, i));
-    double s = p.s_other;
-    if (L::conserved(k)) s = 0.0;
-    if (L::stress(k)) s = omega;
-    r[k] = (float)((1.0 - s) / D);
-  }
-}
-
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -499,8 +486,8 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   k.T_hot = (float)p.T_hot;
   k.objective = p.objective;
   if (p.collision == LBM_MRT) {
-    if (p.lattice == LBM_D3Q19) mrt_rates<albm::D3Q19>(p, (float)omega, k.mrt_r);
-    else mrt_rates<albm::D2Q9>(p, (float)omega, k.mrt_r);
+    if (p.lattice == LBM_D3Q19) albm::fill_mrt<albm::D3Q19>(omega, p.s_other, k);
+    else albm::fill_mrt<albm::D2Q9>(omega, p.s_other, k);
   }
   h->state_bytes = (size_t)h->M * (size_t)h->N * (size_t)h->ks.storage_bytes;
   // time weights c_n of J = sum_n c_n F(f^n)

@@ -150,19 +150,6 @@ cudaError_t dispatch(const lbm_params& p, const albm::KParams& P, const float* f
   }
 }
 
-template <class L>
-void rates(const lbm_params& p, float omega, float* r) {
-  for (int k = 0; k < 19; ++k) r[k] = 0.f;
-  for (int k = 0; k < L::NMOM; ++k) {
-    double D = 0.0;
-    for (int i = 0; i < L::Q; ++i) D += double(L::U(k, i)) * double(L::U(k, i));
-    double s = p.s_other;
-    if (L::conserved(k)) s = 0.0;
-    if (L::stress(k)) s = omega;
-    r[k] = (float)((1.0 - s) / D);
-  }
-}
-
 lbm_status fail(lbm_status code, const std::string& msg) {
   g_err = msg;
   return code;
@@ -238,8 +225,8 @@ extern "C" lbm_status lbm_state_objective_noalloc(const lbm_params* pp, const fl
   P.inv_A_in = 1.0f;   // inlet terms are summed unscaled and divided by the count below
   P.inv_A_out = 0.0f;
   if (p.collision == LBM_MRT) {
-    if (p.lattice == LBM_D3Q19) rates<albm::D3Q19>(p, (float)omega, P.mrt_r);
-    else rates<albm::D2Q9>(p, (float)omega, P.mrt_r);
+    if (p.lattice == LBM_D3Q19) albm::fill_mrt<albm::D3Q19>(omega, p.s_other, P);
+    else albm::fill_mrt<albm::D2Q9>(omega, p.s_other, P);
   }
   cudaStream_t st = (cudaStream_t)stream;
   e = dispatch(p, P, f, theta, flags, scratch, st);

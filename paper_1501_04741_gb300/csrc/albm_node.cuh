@@ -36,6 +36,10 @@ enum { POR_LINEAR = 0, POR_POWER = 1, POR_RAMP = 2 };
 #ifndef ALBM_ADJ_TWO_PHASE
 #define ALBM_ADJ_TWO_PHASE 1
 #endif
+// MRT through all 19 moments instead of the rank-one form (same operator)
+#ifndef ALBM_MRT_FULL
+#define ALBM_MRT_FULL 0
+#endif
 
 // Constants of one problem, passed by value to every kernel.
 struct KParams {
@@ -51,8 +55,23 @@ struct KParams {
   float T_hot;
   int objective;
   float inv_A_in, inv_A_out;
+  float mrt_diag;
   float mrt_r[19];
 };
+
+// MRT coefficients of NodeOps::mrt_op for rates omega (stress moments),
+// s_other (other non-conserved moments) and 0 (conserved moments)
+template <class L>
+inline void fill_mrt(double omega, double s_other, KParams& k) {
+  for (int j = 0; j < 19; ++j) k.mrt_r[j] = 0.f;
+  k.mrt_diag = (float)(1.0 - s_other);
+  for (int j = 0; j < L::NMOM; ++j) {
+    double D = 0.0;
+    for (int i = 0; i < L::Q; ++i) D += double(L::U(j, i)) * double(L::U(j, i));
+    if (L::stress(j)) k.mrt_r[j] = (float)((s_other - omega) / D);
+    if (L::conserved(j)) k.mrt_r[j] = (float)(s_other / D);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // porosity G(theta) (Sec. 3.2, theta = 1 - w) and diffusivity interpolation
@@ -91,27 +110,62 @@ struct NodeOps {
   static constexpr int M = Q + NS * QS;
   static constexpr int NSA = NS > 0 ? NS : 1;
 
-  // y = U^-1 (I - T) U x  (symmetric; fully unrolled, constant U folded)
+  // y = U^-1 (I - T) U x.  U has orthogonal rows, so U^-1 = U^T D^-1 and
+  // sum_k U_k U_k^T / D_k = I; all non-stress, non-conserved moments share
+  // one rate s, hence
+  //   U^-1 (I - T) U = (1 - s) I + sum_{k stress, conserved} c_k U_k U_k^T,
+  //   c_k = (s - s_k) / D_k   (s_k = omega for stress moments, 0 for rho, j),
+  // a symmetric operator needing 9 (D3Q19) or 5 (D2Q9) moments, not 19 / 9.
+  // P.mrt_r[k] holds c_k and P.mrt_diag holds 1 - s (set by fill_mrt).
   __device__ static __forceinline__ void mrt_op(const KParams& P, const float* x, float* y) {
-    float m[L::NMOM];
+#if ALBM_MRT_FULL
+    // the same operator through all moments: y = sum_k r_k U_k (U_k . x)
+    float mf[L::NMOM];
 #pragma unroll
     for (int k = 0; k < L::NMOM; ++k) {
-      float s = 0.0f;
+      float a = 0.0f;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        if (L::U(k, i) != 0) s += float(L::U(k, i)) * x[i];
-      }
-      m[k] = s * P.mrt_r[k];
+      for (int i = 0; i < Q; ++i)
+        if (L::U(k, i) != 0) a += float(L::U(k, i)) * x[i];
+      const float D = float(Dsq(k));
+      const float rk = L::stress(k) ? (P.mrt_diag + P.mrt_r[k] * D)
+                                    : (L::conserved(k) ? (P.mrt_diag + P.mrt_r[k] * D) : P.mrt_diag);
+      mf[k] = a * rk / D;
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      float s = 0.0f;
+      float v = 0.0f;
 #pragma unroll
-      for (int k = 0; k < L::NMOM; ++k) {
-        if (L::U(k, i) != 0) s += float(L::U(k, i)) * m[k];
-      }
-      y[i] = s;
+      for (int k = 0; k < L::NMOM; ++k)
+        if (L::U(k, i) != 0) v += float(L::U(k, i)) * mf[k];
+      y[i] = v;
     }
+    return;
+#endif
+    float m[L::NMOM];
+#pragma unroll
+    for (int k = 0; k < L::NMOM; ++k) {
+      m[k] = 0.0f;
+      if (!(L::stress(k) || L::conserved(k))) continue;
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        if (L::U(k, i) != 0) m[k] += float(L::U(k, i)) * x[i];
+      m[k] *= P.mrt_r[k];
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      float v = P.mrt_diag * x[i];
+#pragma unroll
+      for (int k = 0; k < L::NMOM; ++k)
+        if ((L::stress(k) || L::conserved(k)) && L::U(k, i) != 0) v += float(L::U(k, i)) * m[k];
+      y[i] = v;
+    }
+  }
+
+  __host__ __device__ static constexpr int Dsq(int k) {
+    int d = 0;
+    for (int i = 0; i < Q; ++i) d += L::U(k, i) * L::U(k, i);
+    return d;
   }
 
   // Zou-He (Sec. 3): reconstruct the unknown populations of an x face in
