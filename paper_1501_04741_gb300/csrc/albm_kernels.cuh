@@ -24,10 +24,10 @@
 namespace albm {
 
 // ---- launch tunables (minimum resident blocks per SM of 256 threads) -----
-// primal: 8 blocks of 128 threads per SM (64 registers) measured ~7 % faster
-// than 4 blocks of 256 on the steps that record the objective
+// primal: 7 blocks of 128 threads per SM (73 registers, no spills) measured
+// fastest among 4x256, 5x256, 8x128 (64 registers, small spills) and 7x128
 #ifndef ALBM_PRIMAL_MINB
-#define ALBM_PRIMAL_MINB 8
+#define ALBM_PRIMAL_MINB 7
 #endif
 #ifndef ALBM_PRIMAL_BLOCK
 #define ALBM_PRIMAL_BLOCK 128
