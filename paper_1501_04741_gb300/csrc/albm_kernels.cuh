@@ -33,12 +33,13 @@ namespace albm {
 #define ALBM_PRIMAL_BLOCK 128
 #endif
 #ifndef ALBM_ADJOINT_MINB
-#define ALBM_ADJOINT_MINB 4
+#define ALBM_ADJOINT_MINB 8
 #endif
-// threads per block of the single-instance adjoint kernel (4 blocks of 128
-// per SM at its ~119 registers measured 4 % faster than 2 blocks of 256)
+// threads per block of the single-instance adjoint kernel: at its ~119
+// registers 16 warps fit an SM; 8 blocks of 64 measured 1 % faster than 4 of
+// 128 and 5 % faster than 2 of 256 (tighter caps spill and lose)
 #ifndef ALBM_ADJ_BLOCK
-#define ALBM_ADJ_BLOCK 128
+#define ALBM_ADJ_BLOCK 64
 #endif
 // streaming (evict-first) stores for the state and adjoint outputs, which
 // the same kernel never reads back
