@@ -49,6 +49,13 @@ def bytes_per_node(M: int, storage: int, kind: str) -> int:
     return M * 4 * 2 + M * storage + 21
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu capture of the 256x128x64 profile case, scaled by the node count to
+# the 256x128x128 lattice (traffic grows with the nodes); valid for the FP32
+# mixer kernels as captured (profiles/*_kernel_mixer3d_256x128x64.md).
+TRAFFIC_MIXER_FP32 = {"primal": 1.0336e9, "adjoint": 1.6781e9}
+
+
 def workload(args) -> inputs.Problem:
     P = inputs.exchanger3d() if args.workload == "exchanger3d" else inputs.mixer3d()
     if args.nsteps:
@@ -296,7 +303,12 @@ def run_ours(args):
             "data": "synthetic", "config": _config(P, args),
             "roofline": {"bound": "hbm", "kernel": f"{dom}_kernel", "achieved": ach,
                          "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "peak_source": peak_kind, "traffic": None},
+                         "peak_source": peak_kind,
+                         "traffic": (TRAFFIC_MIXER_FP32[dom] if (args.workload == "mixer3d" and
+                                                                 P.precision == "fp32" and
+                                                                 P.kernel == "auto" and
+                                                                 not args.nsteps) else None),
+                         "algorithmic_bytes": (bp if dom == "primal" else ba) * N},
             "kernels": {
                 "primal": {"launches": n_p + n_r, "avg_ms": prim_ms, "GB_s": prim_gbs,
                            "bytes_per_node": bp, "MLUPS": N / (prim_ms / 1e3) / 1e6},

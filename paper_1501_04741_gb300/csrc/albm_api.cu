@@ -229,10 +229,10 @@ static StepArgs blank_args(lbm_ctx* h) {
 }
 
 namespace albm {
-__global__ void __launch_bounds__(256) fold_partials_kernel(const double* __restrict__ partials,
-                                                            long long nblocks,
-                                                            double* __restrict__ out) {
-  __shared__ double sh[2][256];
+__global__ void __launch_bounds__(1024) fold_partials_kernel(const double* __restrict__ partials,
+                                                             long long nblocks,
+                                                             double* __restrict__ out) {
+  __shared__ double sh[2][1024];
   double a = 0.0, b = 0.0;
   for (long long i = threadIdx.x; i < nblocks; i += blockDim.x) {
     a += partials[2 * i];
@@ -269,8 +269,8 @@ static lbm_status check_timeout(lbm_ctx* h) {
 
 // fold the per-block partials of step t into the objective record
 static lbm_status fold_objective(lbm_ctx* h, int t, long long count) {
-  albm::fold_partials_kernel<<<1, 256, 0, h->stream>>>(h->partials, count,
-                                                        h->stats + 2 * (size_t)t);
+  albm::fold_partials_kernel<<<1, 1024, 0, h->stream>>>(h->partials, count,
+                                                         h->stats + 2 * (size_t)t);
   h->launches_other++;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "objective fold launch: %s", cudaGetErrorString(e));

@@ -130,7 +130,7 @@ __device__ __forceinline__ void block_partial2(double a, double b, double* out) 
 }
 
 // out[k] = sum over blocks of partials[2 b + k], one block, fixed order
-__global__ void __launch_bounds__(256) fold_partials_kernel(const double* __restrict__ partials,
+__global__ void __launch_bounds__(1024) fold_partials_kernel(const double* __restrict__ partials,
                                                             long long nblocks,
                                                             double* __restrict__ out);
 
