@@ -192,6 +192,109 @@ __global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK, ALBM_PRIMAL_MINB) primal_ke
                              (long long)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// primal step for 16-bit storage, two nodes (2k, 2k+1) of a row per thread:
+// every gather and store moves a 4-byte pair.  For a density with e_x = 0
+// the pair is one aligned word; with e_x = +1 (source x - 1) it is the high
+// half of the word before and the low half of the word at 2k, with e_x = -1
+// the high half of the word at 2k and the low half of the next word (the
+// words wrap at the ends of the row: periodic x).  Needs nx even.
+// ---------------------------------------------------------------------------
+template <class S> struct Pair;
+template <> struct Pair<__nv_bfloat16> {
+  using W = __nv_bfloat162;
+  __device__ static __forceinline__ float2 ld(const __nv_bfloat16* p) {
+    return __bfloat1622float2(__ldg(reinterpret_cast<const W*>(p)));
+  }
+  __device__ static __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
+    *reinterpret_cast<W*>(p) = __floats2bfloat162_rn(a, b);
+  }
+};
+template <> struct Pair<__half> {
+  using W = __half2;
+  __device__ static __forceinline__ float2 ld(const __half* p) {
+    return __half22float2(__ldg(reinterpret_cast<const W*>(p)));
+  }
+  __device__ static __forceinline__ void st(__half* p, float a, float b) {
+    *reinterpret_cast<W*>(p) = __floats2half2_rn(a, b);
+  }
+};
+
+template <class S>
+__device__ __forceinline__ void gather_pair(const S* rowp, int ex, int x, int nx, float& a, float& b) {
+  if (ex == 0) {
+    const float2 w = Pair<S>::ld(rowp + x);
+    a = w.x;
+    b = w.y;
+  } else if (ex > 0) {  // sources x - 1, x
+    const float2 w0 = Pair<S>::ld(rowp + (x == 0 ? nx - 2 : x - 2));
+    const float2 w1 = Pair<S>::ld(rowp + x);
+    a = w0.y;
+    b = w1.x;
+  } else {              // sources x + 1, x + 2
+    const float2 w1 = Pair<S>::ld(rowp + x);
+    const float2 w2 = Pair<S>::ld(rowp + (x + 2 == nx ? 0 : x + 2));
+    a = w1.y;
+    b = w2.x;
+  }
+}
+
+template <class L, int NS, bool MRT, class S>
+__device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __restrict__ Bin,
+                                                 S* __restrict__ Bout, const float* __restrict__ theta,
+                                                 const uint8_t* __restrict__ flags,
+                                                 double* __restrict__ obj, long long pair, int block) {
+  using Ops = NodeOps<L, NS, MRT>;
+  using LS = typename Ops::LS;
+  constexpr int Q = Ops::Q, QS = Ops::QS, NSA = Ops::NSA;
+  double o1 = 0.0, o2 = 0.0;
+  const int hx = P.nx >> 1;
+  if (pair < P.N / 2) {
+    const long long row = pair / hx;
+    const int x = 2 * (int)(pair - row * hx);
+    const int y = (int)(row % P.ny), z = (int)(row / P.ny);
+    const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? P.nz - 1 : z - 1, zp = z == P.nz - 1 ? 0 : z + 1;
+    auto rowoff = [&](int ey, int ez) -> long long {  // source row of shift (ey, ez)
+      const int ys = ey > 0 ? ym : (ey < 0 ? yp : y);
+      const int zs = ez > 0 ? zm : (ez < 0 ? zp : z);
+      return ((long long)zs * P.ny + ys) * P.nx;
+    };
+    float da[Q], db[Q], ga[NSA][QS], gb[NSA][QS];
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      gather_pair<S>(Bin + (long long)i * P.N + rowoff(L::ey(i), L::ez(i)), L::ex(i), x, P.nx, da[i],
+                     db[i]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < QS; ++i)
+        gather_pair<S>(Bin + (long long)(Q + s * QS + i) * P.N + rowoff(LS::ey(i), LS::ez(i)),
+                       LS::ex(i), x, P.nx, ga[s][i], gb[s][i]);
+    const long long idx = row * P.nx + x;
+    const float2 th = *reinterpret_cast<const float2*>(theta + idx);
+    const uint8_t ta = flags[idx], tb = flags[idx + 1];
+    Ops::forward(P, ta, th.x, y, da, ga, obj != nullptr, o1, o2);
+    Ops::forward(P, tb, th.y, y, db, gb, obj != nullptr, o1, o2);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Pair<S>::st(Bout + (long long)i * P.N + idx, da[i], db[i]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < QS; ++i)
+        Pair<S>::st(Bout + (long long)(Q + s * QS + i) * P.N + idx, ga[s][i], gb[s][i]);
+  }
+  if (obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
+}
+
+template <class L, int NS, bool MRT, class S>
+__global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK, 4) primal_pair_kernel(
+    KParams P, const S* __restrict__ Bin, S* __restrict__ Bout, const float* __restrict__ theta,
+    const uint8_t* __restrict__ flags, double* __restrict__ obj) {
+  primal_pair_body<L, NS, MRT, S>(P, Bin, Bout, theta, flags, obj,
+                                  (long long)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
+}
+
 // objective terms of f^n only (no state write), used for F(f^N)
 template <class L, int NS, bool MRT, class S>
 __global__ void __launch_bounds__(256) objective_kernel(KParams P, const S* __restrict__ Bin,
@@ -465,7 +568,17 @@ constexpr int kBlock = 256;
 template <class L, int NS, bool MRT, class S>
 struct Launch {
   static unsigned blocks(const KParams& P) { return (unsigned)((P.N + kBlock - 1) / kBlock); }
+  // 16-bit storage with an even nx runs two nodes per thread
+  static bool paired(const KParams& P) { return sizeof(S) == 2 && (P.nx % 2) == 0; }
   static cudaError_t primal(const KParams& P, const StepArgs& a, cudaStream_t st) {
+    if constexpr (sizeof(S) == 2) {
+      if (paired(P)) {
+        const unsigned nb = (unsigned)((P.N / 2 + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK);
+        primal_pair_kernel<L, NS, MRT, S><<<nb, ALBM_PRIMAL_BLOCK, 0, st>>>(
+            P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags, a.obj);
+        return cudaGetLastError();
+      }
+    }
     const unsigned nb = (unsigned)((P.N + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK);
     primal_kernel<L, NS, MRT, S><<<nb, ALBM_PRIMAL_BLOCK, 0, st>>>(
         P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags, a.obj);
@@ -566,7 +679,8 @@ struct Launch {
     return cudaGetLastError();
   }
   static long long primal_partials(const KParams& P) {
-    return (P.N + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK;
+    const long long threads = paired(P) ? P.N / 2 : P.N;
+    return (threads + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK;
   }
   static KernelSet set() {
     return KernelSet{&primal, &objective, &adjoint, &exportf, &importf, &nonfinite,

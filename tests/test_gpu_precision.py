@@ -27,9 +27,15 @@ def _cases():
     # horizons long enough for the inlet scalar to reach the outlet (x / u_in
     # steps), so that the outlet objectives are not made of values below the
     # FP16 normal range (6.1e-5), which it stores with coarse absolute steps
+    # odd nx runs the one-node-per-thread kernels, even nx the paired
+    # 16-bit primal (two nodes per thread, 4-byte pair gathers and stores)
     mix = inputs.scaled(inputs.mixer3d(), (21, 11, 10), nsteps=500, obj_window=50)
     exch = inputs.scaled(inputs.exchanger3d(), (23, 10, 9), nsteps=300)
-    return {"mixer3d_mrt": mix, "exchanger3d_bgk": exch}
+    return {"mixer3d_mrt": mix, "exchanger3d_bgk": exch,
+            "mixer3d_mrt_even_nx": mix.replace(dims=(22, 11, 10)),
+            "exchanger3d_bgk_even_nx": exch.replace(dims=(24, 10, 9)),
+            "channel2d_even_nx": inputs.channel2d(dims=(40, 21, 1), design=(10, 30, 4, 17, 0, 1),
+                                                  nsteps=300, force=(1e-4, 0, 0))}
 
 
 CASES = _cases()
