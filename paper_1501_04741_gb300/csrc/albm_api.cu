@@ -452,8 +452,7 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   h->stream = (cudaStream_t)stream;
   bool ok = p.lattice == LBM_D2Q9
                 ? albm::kernels_d2q9(p.collision, p.nscalars, p.precision, &h->ks)
-                : (p.collision == LBM_MRT ? albm::kernels_d3q19_mrt(p.nscalars, p.precision, &h->ks)
-                                          : albm::kernels_d3q19_bgk(p.nscalars, p.precision, &h->ks));
+                : albm::kernels_d3q19(p.collision == LBM_MRT, p.nscalars, p.precision, &h->ks);
   if (!ok) {
     *out = h;
     h->err = "no kernel for this lattice/collision/scalars/precision";

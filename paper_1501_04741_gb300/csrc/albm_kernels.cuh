@@ -32,6 +32,15 @@ namespace albm {
 #ifndef ALBM_PRIMAL_BLOCK
 #define ALBM_PRIMAL_BLOCK 128
 #endif
+// resident blocks of the primal kernel on steps that record no objective:
+// 8 (64 registers, no spills) with at most one scalar lattice, measured 2 %
+// faster on the exchanger; with two scalars 8 blocks spill and lose 6 %
+#ifndef ALBM_PRIMAL_MINB_NOOBJ
+#define ALBM_PRIMAL_MINB_NOOBJ 8
+#endif
+#ifndef ALBM_PRIMAL_MINB_NOOBJ_NS2
+#define ALBM_PRIMAL_MINB_NOOBJ_NS2 7
+#endif
 #ifndef ALBM_ADJOINT_MINB
 #define ALBM_ADJOINT_MINB 8
 #endif
@@ -41,12 +50,15 @@ namespace albm {
 #ifndef ALBM_ADJ_BLOCK
 #define ALBM_ADJ_BLOCK 64
 #endif
+// resident blocks of the adjoint kernel without objective sources
+#ifndef ALBM_ADJOINT_MINB_NOSRC
+#define ALBM_ADJOINT_MINB_NOSRC 8
+#endif
 // streaming (evict-first) stores for the state and adjoint outputs, which
 // the same kernel never reads back
 #ifndef ALBM_STREAM_STORES
 #define ALBM_STREAM_STORES 0
 #endif
-
 // ---- storage conversions -------------------------------------------------
 __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
@@ -157,7 +169,9 @@ struct Gather {
 // ---------------------------------------------------------------------------
 // primal step: B^{n+1}(x) = W^x(f^n(x)); optional objective terms of f^n
 // ---------------------------------------------------------------------------
-template <class L, int NS, bool MRT, class S>
+// OBJ = false: the step records no objective (obj is null); the objective
+// terms and the block reduction are compiled out.
+template <class L, int NS, bool MRT, class S, bool OBJ = true>
 __device__ __forceinline__ void primal_body(const KParams& P, const S* __restrict__ Bin,
                                             S* __restrict__ Bout, const float* __restrict__ theta,
                                             const uint8_t* __restrict__ flags,
@@ -171,7 +185,7 @@ __device__ __forceinline__ void primal_body(const KParams& P, const S* __restric
     Gather<L, NS, S>::pre(geo, P.N, Bin, d, g);
     const uint8_t type = flags[idx];
     const float th = theta[idx];
-    Ops::forward(P, type, th, geo.y, d, g, obj != nullptr, o1, o2);
+    Ops::forward(P, type, th, geo.y, d, g, OBJ && obj != nullptr, o1, o2);
 #pragma unroll
     for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, d[i]);
 #pragma unroll
@@ -179,17 +193,20 @@ __device__ __forceinline__ void primal_body(const KParams& P, const S* __restric
 #pragma unroll
       for (int i = 0; i < QS; ++i) st(Bout + (long long)(Q + s * QS + i) * P.N + idx, g[s][i]);
   }
-  if (obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
+  if (OBJ && obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
 }
 
-template <class L, int NS, bool MRT, class S>
-__global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK, ALBM_PRIMAL_MINB) primal_kernel(KParams P, const S* __restrict__ Bin,
+template <class L, int NS, bool MRT, class S, bool OBJ>
+__global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK,
+                                  OBJ ? ALBM_PRIMAL_MINB
+                                      : (NS >= 2 ? ALBM_PRIMAL_MINB_NOOBJ_NS2 : ALBM_PRIMAL_MINB_NOOBJ))
+    primal_kernel(KParams P, const S* __restrict__ Bin,
                                                      S* __restrict__ Bout,
                                                      const float* __restrict__ theta,
                                                      const uint8_t* __restrict__ flags,
                                                      double* __restrict__ obj) {
-  primal_body<L, NS, MRT, S>(P, Bin, Bout, theta, flags, obj,
-                             (long long)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
+  primal_body<L, NS, MRT, S, OBJ>(P, Bin, Bout, theta, flags, obj,
+                                  (long long)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -239,7 +256,7 @@ __device__ __forceinline__ void gather_pair(const S* rowp, int ex, int x, int nx
   }
 }
 
-template <class L, int NS, bool MRT, class S>
+template <class L, int NS, bool MRT, class S, bool OBJ = true>
 __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __restrict__ Bin,
                                                  S* __restrict__ Bout, const float* __restrict__ theta,
                                                  const uint8_t* __restrict__ flags,
@@ -274,8 +291,8 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
     const long long idx = row * P.nx + x;
     const float2 th = *reinterpret_cast<const float2*>(theta + idx);
     const uint8_t ta = flags[idx], tb = flags[idx + 1];
-    Ops::forward(P, ta, th.x, y, da, ga, obj != nullptr, o1, o2);
-    Ops::forward(P, tb, th.y, y, db, gb, obj != nullptr, o1, o2);
+    Ops::forward(P, ta, th.x, y, da, ga, OBJ && obj != nullptr, o1, o2);
+    Ops::forward(P, tb, th.y, y, db, gb, OBJ && obj != nullptr, o1, o2);
 #pragma unroll
     for (int i = 0; i < Q; ++i) Pair<S>::st(Bout + (long long)i * P.N + idx, da[i], db[i]);
 #pragma unroll
@@ -284,15 +301,15 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
       for (int i = 0; i < QS; ++i)
         Pair<S>::st(Bout + (long long)(Q + s * QS + i) * P.N + idx, ga[s][i], gb[s][i]);
   }
-  if (obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
+  if (OBJ && obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
 }
 
-template <class L, int NS, bool MRT, class S>
+template <class L, int NS, bool MRT, class S, bool OBJ>
 __global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK, 4) primal_pair_kernel(
     KParams P, const S* __restrict__ Bin, S* __restrict__ Bout, const float* __restrict__ theta,
     const uint8_t* __restrict__ flags, double* __restrict__ obj) {
-  primal_pair_body<L, NS, MRT, S>(P, Bin, Bout, theta, flags, obj,
-                                  (long long)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
+  primal_pair_body<L, NS, MRT, S, OBJ>(P, Bin, Bout, theta, flags, obj,
+                                       (long long)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.x);
 }
 
 // objective terms of f^n only (no state write), used for F(f^N)
@@ -323,7 +340,7 @@ __global__ void __launch_bounds__(256) objective_kernel(KParams P, const S* __re
 // ---------------------------------------------------------------------------
 // adjoint step: lambda^n(x) from lambda^{n+1}(x + e_j) and f^n(x)
 // ---------------------------------------------------------------------------
-template <class L, int NS, bool MRT, class S>
+template <class L, int NS, bool MRT, class S, bool SRC = true>
 __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __restrict__ lam_in,
                                              const S* __restrict__ Bn, float* __restrict__ lam_out,
                                              const float* __restrict__ theta,
@@ -363,7 +380,8 @@ __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __re
     }
   };
   float lam[Q], lamg[NSA][QS], dth;
-  Ops::reverse(P, type, theta[idx], geo.y, d, g, load, ws, cbar, lam, lamg, dth);
+  Ops::template reverse<decltype(load), SRC>(P, type, theta[idx], geo.y, d, g, load, ws, cbar, lam,
+                                             lamg, dth);
 #pragma unroll
   for (int i = 0; i < Q; ++i) st(lam_out + (long long)i * P.N + idx, lam[i]);
 #pragma unroll
@@ -373,8 +391,11 @@ __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __re
   if (type == FLUID || type == INLET || type == OUTLET) grad[idx] += (double)dth;
 }
 
-template <class L, int NS, bool MRT, class S>
-__global__ void __launch_bounds__(ALBM_ADJ_BLOCK, ALBM_ADJOINT_MINB) adjoint_kernel(KParams P, const float* __restrict__ lam_in,
+// SRC: the step carries an objective source (ws != 0); most steps of a long
+// horizon with a short objective window do not, and the kernel without the
+// source terms holds fewer registers across the lambda gathers
+template <class L, int NS, bool MRT, class S, bool SRC>
+__global__ void __launch_bounds__(ALBM_ADJ_BLOCK, SRC ? ALBM_ADJOINT_MINB : ALBM_ADJOINT_MINB_NOSRC) adjoint_kernel(KParams P, const float* __restrict__ lam_in,
                                                       const S* __restrict__ Bn,
                                                       float* __restrict__ lam_out,
                                                       const float* __restrict__ theta,
@@ -382,8 +403,8 @@ __global__ void __launch_bounds__(ALBM_ADJ_BLOCK, ALBM_ADJOINT_MINB) adjoint_ker
                                                       double* __restrict__ grad, float ws,
                                                       const double* __restrict__ stat_n,
                                                       int has_next) {
-  adjoint_body<L, NS, MRT, S>(P, lam_in, Bn, lam_out, theta, flags, grad, ws, stat_n, has_next,
-                              (long long)blockIdx.x * blockDim.x + threadIdx.x);
+  adjoint_body<L, NS, MRT, S, SRC>(P, lam_in, Bn, lam_out, theta, flags, grad, ws, stat_n, has_next,
+                                   (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -429,16 +450,28 @@ template <class L, int NS, bool MRT, class S>
 __global__ void __launch_bounds__(256, 4) primal_batch_kernel(const __grid_constant__ BatchArgs args) {
   const InstanceDesc& D = args.inst[batch_instance(args)];
   const int block = (int)((long long)blockIdx.x - D.block_begin);
-  primal_body<L, NS, MRT, S>(D.P, (const S*)D.Bin, (S*)D.Bout, D.theta, D.flags, D.obj,
-                             (long long)block * blockDim.x + threadIdx.x, block);
+  const long long idx = (long long)block * blockDim.x + threadIdx.x;
+  // the same specialisation as the single-instance launch of this step, so
+  // that batched and lone results agree bit for bit
+  if (D.obj != nullptr)
+    primal_body<L, NS, MRT, S, true>(D.P, (const S*)D.Bin, (S*)D.Bout, D.theta, D.flags, D.obj, idx,
+                                     block);
+  else
+    primal_body<L, NS, MRT, S, false>(D.P, (const S*)D.Bin, (S*)D.Bout, D.theta, D.flags, D.obj,
+                                      idx, block);
 }
 
 template <class L, int NS, bool MRT, class S>
 __global__ void __launch_bounds__(256, 2) adjoint_batch_kernel(const __grid_constant__ BatchArgs args) {
   const InstanceDesc& D = args.inst[batch_instance(args)];
   const long long block = (long long)blockIdx.x - D.block_begin;
-  adjoint_body<L, NS, MRT, S>(D.P, D.lam_in, (const S*)D.Bin, D.lam_out, D.theta, D.flags, D.grad,
-                              D.ws, D.stat_n, D.has_next, block * blockDim.x + threadIdx.x);
+  const long long idx = block * blockDim.x + threadIdx.x;
+  if (D.ws != 0.0f)
+    adjoint_body<L, NS, MRT, S, true>(D.P, D.lam_in, (const S*)D.Bin, D.lam_out, D.theta, D.flags,
+                                      D.grad, D.ws, D.stat_n, D.has_next, idx);
+  else
+    adjoint_body<L, NS, MRT, S, false>(D.P, D.lam_in, (const S*)D.Bin, D.lam_out, D.theta, D.flags,
+                                       D.grad, D.ws, D.stat_n, D.has_next, idx);
 }
 
 // ---------------------------------------------------------------------------
@@ -574,14 +607,16 @@ struct Launch {
     if constexpr (sizeof(S) == 2) {
       if (paired(P)) {
         const unsigned nb = (unsigned)((P.N / 2 + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK);
-        primal_pair_kernel<L, NS, MRT, S><<<nb, ALBM_PRIMAL_BLOCK, 0, st>>>(
-            P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags, a.obj);
+        auto k = a.obj != nullptr ? primal_pair_kernel<L, NS, MRT, S, true>
+                                  : primal_pair_kernel<L, NS, MRT, S, false>;
+        k<<<nb, ALBM_PRIMAL_BLOCK, 0, st>>>(P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags,
+                                            a.obj);
         return cudaGetLastError();
       }
     }
     const unsigned nb = (unsigned)((P.N + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK);
-    primal_kernel<L, NS, MRT, S><<<nb, ALBM_PRIMAL_BLOCK, 0, st>>>(
-        P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags, a.obj);
+    auto k = a.obj != nullptr ? primal_kernel<L, NS, MRT, S, true> : primal_kernel<L, NS, MRT, S, false>;
+    k<<<nb, ALBM_PRIMAL_BLOCK, 0, st>>>(P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags, a.obj);
     return cudaGetLastError();
   }
   static cudaError_t objective(const KParams& P, const StepArgs& a, cudaStream_t st) {
@@ -591,9 +626,9 @@ struct Launch {
   }
   static cudaError_t adjoint(const KParams& P, const StepArgs& a, cudaStream_t st) {
     const unsigned nb = (unsigned)((P.N + ALBM_ADJ_BLOCK - 1) / ALBM_ADJ_BLOCK);
-    adjoint_kernel<L, NS, MRT, S><<<nb, ALBM_ADJ_BLOCK, 0, st>>>(
-        P, a.lam_in, (const S*)a.Bin, a.lam_out, a.theta, a.flags, a.grad, a.ws, a.stat_n,
-        a.has_next);
+    auto k = a.ws != 0.0f ? adjoint_kernel<L, NS, MRT, S, true> : adjoint_kernel<L, NS, MRT, S, false>;
+    k<<<nb, ALBM_ADJ_BLOCK, 0, st>>>(P, a.lam_in, (const S*)a.Bin, a.lam_out, a.theta, a.flags,
+                                     a.grad, a.ws, a.stat_n, a.has_next);
     return cudaGetLastError();
   }
   static cudaError_t exportf(const KParams& P, const StepArgs& a, cudaStream_t st) {
@@ -689,9 +724,39 @@ struct Launch {
   }
 };
 
-// Lookup of the instantiated set; defined in the per-lattice translation units.
+// The kernel set of one (lattice, collision, storage) for 0..MAXNS scalars.
+template <class L, bool MRT, class S, int MAXNS>
+bool pick_scalars(int nscalars, KernelSet* out) {
+  switch (nscalars) {
+    case 0: *out = Launch<L, 0, MRT, S>::set(); return true;
+    case 1: *out = Launch<L, 1, MRT, S>::set(); return true;
+    case 2:
+      if constexpr (MAXNS >= 2) {
+        *out = Launch<L, 2, MRT, S>::set();
+        return true;
+      }
+      return false;
+    default: return false;
+  }
+}
+
+// Lookup of the instantiated sets, defined in the per-lattice translation
+// units (the D3Q19 ones split by storage type so that they build in parallel).
 bool kernels_d2q9(int collision, int nscalars, int precision, KernelSet* out);
-bool kernels_d3q19_bgk(int nscalars, int precision, KernelSet* out);
-bool kernels_d3q19_mrt(int nscalars, int precision, KernelSet* out);
+bool kernels_d3q19_bgk_f32(int nscalars, KernelSet* out);
+bool kernels_d3q19_bgk_bf16(int nscalars, KernelSet* out);
+bool kernels_d3q19_bgk_f16(int nscalars, KernelSet* out);
+bool kernels_d3q19_mrt_f32(int nscalars, KernelSet* out);
+bool kernels_d3q19_mrt_bf16(int nscalars, KernelSet* out);
+bool kernels_d3q19_mrt_f16(int nscalars, KernelSet* out);
+
+inline bool kernels_d3q19(bool mrt, int nscalars, int precision, KernelSet* out) {
+  switch (precision) {
+    case 0: return mrt ? kernels_d3q19_mrt_f32(nscalars, out) : kernels_d3q19_bgk_f32(nscalars, out);
+    case 1: return mrt ? kernels_d3q19_mrt_bf16(nscalars, out) : kernels_d3q19_bgk_bf16(nscalars, out);
+    case 2: return mrt ? kernels_d3q19_mrt_f16(nscalars, out) : kernels_d3q19_bgk_f16(nscalars, out);
+    default: return false;
+  }
+}
 
 }  // namespace albm

@@ -420,8 +420,10 @@ struct NodeOps {
   // -------------------------------------------------------------------------
   // The adjoint weights are fetched by load(a, b) only after the forward
   // quantities are recomputed (two phases: f^n first, lambda^{n+1} second),
-  // which bounds the number of values live in registers at once.
-  template <class Loader>
+  // which bounds the number of values live in registers at once.  SRC =
+  // false compiles the objective source terms out, for steps whose weight ws
+  // is zero (same values: the sources only add exact zeros then).
+  template <class Loader, bool SRC = true>
   __device__ static __forceinline__ void reverse(const KParams& P, uint8_t type, float th, int y,
                                                  const float* d_in, float (*g)[QS],
                                                  const Loader& load, float ws, float cbar,
@@ -477,7 +479,7 @@ struct NodeOps {
       }
     }
     // ---- objective sources ws * dF^x ----
-    if (ws != 0.0f) {
+    if (SRC && ws != 0.0f) {
       if (P.objective == OBJ_DISSIPATION && type == FLUID) {
         float Pi[3][3];
         pi_neq(d, rho, drho, u, Pi);

@@ -1,0 +1,11 @@
+// Kernel instantiations for the D3Q19 fluid lattice (with D3Q7 scalars),
+// BGK collision, FP16 state storage.
+#include "albm_kernels.cuh"
+
+namespace albm {
+
+bool kernels_d3q19_bgk_f16(int nscalars, KernelSet* out) {
+  return pick_scalars<D3Q19, false, __half, 2>(nscalars, out);
+}
+
+}  // namespace albm
