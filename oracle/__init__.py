@@ -17,7 +17,9 @@ The oracle is plain PyTorch CPU code in float64:
   the primal iteration, the unsteady discrete adjoint (the time-dependent
   form of Eqs. "adjoint:iteration"/"adjoint:operator" with the gradient of
   Eq. "adjoint:derivative" accumulated over the steps), the frozen-state
-  ALBS mode, and a central finite-difference driver.
+  ALBS mode, the one-shot optimisation of Sec. 3.3 with the penalty of
+  Eq. P and the threshold scan of Sec. 3.2, and a central
+  finite-difference driver.
 
 The adjoint collision is the vector-Jacobian product of W^x, taken by
 PyTorch's reverse-mode autodiff (a library primitive, in the role TAPENADE

@@ -24,6 +24,10 @@ are taken by torch.autograd on the step function.
 ``frozen_adjoint`` is the paper's ALBS itself: Eq. "adjoint:iteration"
 iterated at a fixed state f-hat, with the gradient of Eq.
 "adjoint:derivative" evaluated from the final iterate.
+
+``oneshot`` is the one-shot optimisation of Sec. 3.3 (primal, adjoint and
+design updated together, Eq. "gradient:update", with the penalty of Eq. P),
+and ``threshold`` / ``threshold_scan`` the final binarisation of Sec. 3.2.
 """
 from __future__ import annotations
 
@@ -123,6 +127,8 @@ class Oracle:
         Fv = F.detach().requires_grad_(True)
         th = self.theta.detach().requires_grad_(True)
         val = weight * self.F_obj(Fv, th)
+        if not val.requires_grad:          # objective "none"
+            return torch.zeros_like(Fv).detach(), torch.zeros_like(th).detach()
         gF, gth = torch.autograd.grad(val, (Fv, th), allow_unused=True)
         if gF is None:
             gF = torch.zeros_like(Fv)
@@ -180,6 +186,95 @@ class Oracle:
             v = v_next + src
         _, gth = self.adjoint_step(v, F_hat)
         return (gth + gth_direct).view(self.shape), v
+
+    # --- one-shot optimisation (Sec. 3.3) -----------------------------------
+    def oneshot(self, iters, zeta, penalty=0.0, maximize=True, design=None, F0=None,
+                v0=None):
+        """The one-shot descent of Sec. 3.3 on theta (solid fraction).
+
+        Iteration k, in the paper's order:
+          1. one LLBS step (Eq. normal:iteration):     f^{k+1} = S W(f^k, theta^k)
+          2. one ALBS step (Eq. adjoint:iteration) at the current primal state:
+                                    v^{k+1} = (d(SW)/df(f^k))^T v^k + dF/df(f^k)
+          3. the gradient estimate of Eq. adjoint:derivative from the adjoint
+             iterate that step 2 consumes:
+                                    g^k = (d(SW)/dtheta(f^k))^T v^k + dF/dtheta(f^k)
+          4. the update of Eq. gradient:update with the penalty P of Eq. P,
+             P = sum theta (1 - theta), on design nodes only:
+                 theta^{k+1} = clip(theta^k + zeta (s g^k - penalty (1 - 2 theta^k)), 0, 1)
+             with s = +1 when J is maximised, -1 when it is minimised (the
+             penalty term always lowers P).
+
+        Returns (theta^K as float64 (Lz, Ly, Lx), f^K, v^K, g^{K-1}).
+        """
+        th = self.theta.clone()
+        mask = (torch.ones(self.n, dtype=torch.bool) if design is None else
+                torch.as_tensor(np.asarray(design).reshape(-1).astype(bool)))
+        s = 1.0 if maximize else -1.0
+        F = self.initial() if F0 is None else F0
+        v = torch.zeros_like(F) if v0 is None else v0
+        g = torch.zeros(self.n, dtype=DT)
+        saved = self.theta
+        try:
+            for _ in range(int(iters)):
+                self.theta = th
+                with torch.no_grad():
+                    F_next = self.step(F)
+                gF, gth = self.adjoint_step(v, F)
+                src, gth_direct = self.source(F, 1.0)
+                v_next = gF + src
+                g = gth + gth_direct
+                th = self.design_update(th, g, zeta, penalty, s, mask)
+                F, v = F_next, v_next
+        finally:
+            self.theta = saved
+        return th.view(self.shape), F, v, g.view(self.shape)
+
+    @staticmethod
+    def design_update(th, g, zeta, penalty, s, mask):
+        """Eq. gradient:update on the penalised objective s J - penalty P,
+        d(P)/d(theta) = 1 - 2 theta, kept in [0, 1], design nodes only."""
+        d = s * g - penalty * (1.0 - 2.0 * th)
+        return torch.where(mask, torch.clamp(th + zeta * d, 0.0, 1.0), th)
+
+    def penalty(self, theta, design=None):
+        """P of Eq. P over the design nodes."""
+        th = torch.as_tensor(np.asarray(theta, dtype=np.float64).reshape(-1))
+        if design is not None:
+            th = th[torch.as_tensor(np.asarray(design).reshape(-1).astype(bool))]
+        return float((th * (1.0 - th)).sum())
+
+    def steady_objective(self, nsteps, theta=None):
+        """F(f^N) of the primal run of N steps from rest (the objective of
+        the converged flow when N is long enough)."""
+        saved = self.theta
+        try:
+            if theta is not None:
+                self.theta = torch.as_tensor(np.asarray(theta, dtype=np.float64).reshape(-1))
+            F = self.initial()
+            with torch.no_grad():
+                for _ in range(int(nsteps)):
+                    F = self.step(F)
+                return float(self.F_obj(F))
+        finally:
+            self.theta = saved
+
+    @staticmethod
+    def threshold(theta, eta, design=None):
+        """The threshold of Sec. 3.2 on design nodes: w = 1 - theta below eta
+        becomes solid (theta = 1), otherwise fluid (theta = 0).  theta is
+        held in FP32, and w and the comparison are taken in FP32.  A node
+        with w equal to eta is fluid."""
+        th = np.asarray(theta, dtype=np.float32).reshape(-1)
+        mask = np.ones(th.shape, bool) if design is None else np.asarray(design).reshape(-1).astype(bool)
+        w = np.float32(1.0) - th
+        out = th.copy()
+        out[mask] = np.where(w[mask] < np.float32(eta), np.float32(1.0), np.float32(0.0))
+        return out.reshape(np.shape(theta))
+
+    def threshold_scan(self, theta, etas, nsteps, design=None):
+        """F(f^N) of the thresholded design for every level eta."""
+        return [self.steady_objective(nsteps, self.threshold(theta, e, design)) for e in etas]
 
     # --- finite differences -------------------------------------------------
     def fd(self, index, h=1e-6, nsteps=None):

@@ -92,3 +92,89 @@ def test_scalar_using_pre_collision_velocity_is_caught(monkeypatch):
     _mutate(monkeypatch, "macroscopic", bad)
     with pytest.raises(AssertionError):
         TL.test_collision_conserves_mass_and_forced_momentum("BGK", "D2Q9")
+
+
+# ---- one-shot optimisation (Sec. 3.3) -----------------------------------------
+def _oneshot_pins():
+    from tests import test_oracle_oneshot as TO
+    return TO
+
+
+def _converged_case(TO):
+    from oracle.solver import Oracle
+    P = TO._channel()
+    th0 = TO._theta_band(P, 0)
+    mask = inputs.design_mask(P)
+    o = Oracle(P, th0)
+    K = 400
+    th, F, v, g = o.oneshot(K, 0.0, design=mask)
+    return P, th0, mask, o, K, th, F, v, g
+
+
+def test_penalty_pushing_away_from_binary_is_caught(monkeypatch):
+    from oracle.solver import Oracle
+    TO = _oneshot_pins()
+
+    def bad(th, g, zeta, penalty, s, mask):
+        d = s * g + penalty * (1.0 - 2.0 * th)          # sign of dP/dtheta flipped
+        return torch.where(mask, torch.clamp(th + zeta * d, 0.0, 1.0), th)
+    monkeypatch.setattr(Oracle, "design_update", staticmethod(bad))
+    with pytest.raises(AssertionError):
+        TO.test_penalty_alone_follows_closed_form()
+
+
+def test_update_outside_the_design_mask_is_caught(monkeypatch):
+    from oracle.solver import Oracle
+    TO = _oneshot_pins()
+
+    def bad(th, g, zeta, penalty, s, mask):
+        d = s * g - penalty * (1.0 - 2.0 * th)
+        return torch.clamp(th + zeta * d, 0.0, 1.0)     # mask ignored
+    monkeypatch.setattr(Oracle, "design_update", staticmethod(bad))
+    with pytest.raises(AssertionError):
+        TO.test_penalty_alone_follows_closed_form()
+
+
+def test_descending_when_maximising_is_caught(monkeypatch):
+    from oracle.solver import Oracle
+    TO = _oneshot_pins()
+    case = _converged_case(TO)
+
+    def bad(th, g, zeta, penalty, s, mask):
+        d = -s * g - penalty * (1.0 - 2.0 * th)         # step against the objective
+        return torch.where(mask, torch.clamp(th + zeta * d, 0.0, 1.0), th)
+    monkeypatch.setattr(Oracle, "design_update", staticmethod(bad))
+    with pytest.raises(AssertionError):
+        TO.test_one_update_moves_the_objective_by_zeta_g_squared(case, True)
+
+
+def test_gradient_without_the_adjoint_is_caught(monkeypatch):
+    """A gradient estimate that leaves out the adjoint weights (only the
+    direct dF/dtheta, zero for these objectives) fails the FD pin."""
+    from oracle.solver import Oracle
+    TO = _oneshot_pins()
+    orig = Oracle.adjoint_step
+
+    def bad(self, lam_next, F):
+        gF, gth = orig(self, lam_next, F)
+        return gF, torch.zeros_like(gth)
+    monkeypatch.setattr(Oracle, "adjoint_step", bad)
+    case = _converged_case(TO)
+    with pytest.raises(AssertionError):
+        TO.test_zero_step_estimate_is_the_steady_gradient(case)
+
+
+def test_threshold_tie_to_solid_is_caught(monkeypatch):
+    from oracle.solver import Oracle
+    TO = _oneshot_pins()
+
+    def bad(theta, eta, design=None):
+        th = np.asarray(theta, dtype=np.float32).reshape(-1)
+        mask = np.ones(th.shape, bool) if design is None else np.asarray(design).reshape(-1).astype(bool)
+        w = np.float32(1.0) - th
+        out = th.copy()
+        out[mask] = np.where(w[mask] <= np.float32(eta), 1.0, 0.0)   # tie goes solid
+        return out.reshape(np.shape(theta))
+    monkeypatch.setattr(Oracle, "threshold", staticmethod(bad))
+    with pytest.raises(AssertionError):
+        TO.test_threshold_rule()
