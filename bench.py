@@ -16,6 +16,12 @@ state) are larger than L2, so no flush is needed between steps.
 With torchrun (N > 1) every rank solves its own independent replica (the
 path does not shard in this build: replicas only) and rank 0 prints the
 aggregate.
+
+Other workloads (--workload): exchanger3d (512x256x256 BGK + D3Q7, heat
+flux), batch64 (64 instances through the batched autograd Function), serve
+(continuous batching of Poisson-arriving requests), oneshot (the one-shot
+optimisation of Sec. 3.3 on the exchanger) and meshes (primal and adjoint
+kernel rates on the paper's 400K / 3M / 12M scaling meshes).
 """
 from __future__ import annotations
 
@@ -413,6 +419,136 @@ def run_serve(args):
     return 0
 
 
+def run_oneshot(args):
+    """One-shot optimisation (Sec. 3.3) on the full 512x256x256 exchanger:
+    per iteration one primal step, one ALBS step at the current state and the
+    design update, all on the device; node updates counted as 2 per node and
+    iteration (primal + adjoint), as in the headline metric."""
+    import torch
+    from paper_1501_04741_gb300.albm import Solver
+    P = inputs.exchanger3d()
+    if args.precision != "fp32":
+        P = P.replace(precision=args.precision)
+    theta = inputs.theta_grf(P, 0)
+    mask = inputs.design_mask(P).reshape(-1).astype(np.uint8)
+    iters = args.oneshot_iters
+    zeta, pen = 1.0, 1e-4
+    stream = torch.cuda.Stream()
+    s = Solver(P, torch.from_numpy(theta.reshape(-1)).cuda(), stream=stream)
+    N = s.N
+    s.set_design(mask)
+    s.oneshot_reset()
+    for _ in range(args.warmup):
+        s.oneshot_step(iters, zeta, pen, True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    s.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            s.oneshot_step(iters, zeta, pen, True)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    prof = s.profile_read()
+    s.profile(False)
+    clk = clocks.stop()
+    J, Pv = s.oneshot_eval()
+    peak, peak_kind = _peaks()
+    storage = {"fp32": 4, "bf16": 2, "fp16": 2}[P.precision]
+    bp = bytes_per_node(s.M, storage, "primal")
+    ba = bytes_per_node(s.M, storage, "adjoint")
+    (n_p, ms_p), (n_a, ms_a) = prof["primal"], prof["adjoint"]
+    prim_ms, adj_ms = ms_p / max(n_p, 1), ms_a / max(n_a, 1)
+    adj_gbs = ba * N / (adj_ms / 1e3) / 1e9
+    updates = 2.0 * N * iters * args.steps
+    # end to end: host theta and mask in, iterations, J, P and theta out
+    th_host = torch.from_numpy(theta.reshape(-1)).pin_memory()
+    th_out = torch.empty(N, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_theta(th_host.numpy())
+    s.set_design(mask)
+    s.oneshot_reset()
+    s.oneshot_step(iters, zeta, pen, True)
+    s.oneshot_eval()
+    s.theta(th_out)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    print(json.dumps({
+        "metric": "one-shot optimisation primal+adjoint MLUPS", "workload": "oneshot",
+        "value": updates / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "dtype": "f32" if P.precision == "fp32" else f"f32 ({P.precision} storage)",
+        "data": "synthetic",
+        "config": {"workload": "oneshot", "lattice": P.lattice, "collision": P.collision,
+                   "dims": list(P.dims), "nscalars": P.nscalars, "objective": P.objective,
+                   "iterations_per_step": iters, "zeta": zeta, "penalty": pen,
+                   "design_nodes": int(mask.sum()), "l2": "inputs larger than L2 (no flush)"},
+        "iterations_per_s": iters * args.steps / (ms / 1e3),
+        "roofline": {"bound": "hbm", "kernel": "adjoint_kernel", "achieved": adj_gbs,
+                     "peak": peak, "unit": "GB/s", "frac": adj_gbs / peak,
+                     "peak_source": peak_kind, "traffic": None,
+                     "algorithmic_bytes": ba * N},
+        "kernels": {"primal": {"launches": n_p, "avg_ms": prim_ms,
+                               "GB_s": bp * N / (prim_ms / 1e3) / 1e9},
+                    "adjoint": {"launches": n_a, "avg_ms": adj_ms, "GB_s": adj_gbs},
+                    "other_per_iteration_ms": (ms - ms_p - ms_a) / (iters * args.steps)},
+        "J": J, "P": Pv,
+        "e2e": {"value": 2.0 * N * iters / dt / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": int(N * 4 + N), "d2h_bytes_per_step": int(N * 4 + 16)},
+        "gpu_launches": int(prof["launches"]), "clocks": clk}), flush=True)
+    return 0
+
+
+# the paper's scaling meshes (Sec. 4.3): D3Q19 MRT fluid + one D3Q7 scalar,
+# with its one-GPU (Tesla M2090) primal / adjoint MLUPS for context
+MESHES = [("400K", (160, 50, 50), 289, 104), ("3M", (320, 100, 100), 298, 109),
+          ("12M", (320, 200, 200), None, None)]
+
+
+def run_meshes(args):
+    """Primal and adjoint kernel MLUPS on the paper's three scaling meshes
+    (heat-exchanger physics with the MRT fluid collision of Sec. 4), and the
+    adjoint / primal time ratio the paper reports as about 2.65."""
+    import torch
+    from paper_1501_04741_gb300.albm import Solver
+    nsteps = args.nsteps or 200
+    rows = []
+    for name, dims, p_mlups, a_mlups in MESHES:
+        P = inputs.scaled(inputs.exchanger3d(), dims, nsteps=nsteps).replace(collision="MRT")
+        th = torch.from_numpy(inputs.theta_grf(P, 0).reshape(-1)).cuda()
+        with Solver(P, th, stream=torch.cuda.Stream()) as s:
+            for _ in range(args.warmup):
+                s.run()
+            s.profile(True)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                s.run()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            prof = s.profile_read()
+            s.profile(False)
+            N = s.N
+        (n_p, ms_p), (n_r, ms_r), (n_a, ms_a) = prof["primal"], prof["recompute"], prof["adjoint"]
+        prim = N / ((ms_p + ms_r) / max(n_p + n_r, 1) / 1e3) / 1e6
+        adj = N / (ms_a / max(n_a, 1) / 1e3) / 1e6
+        rows.append({"mesh": name, "dims": list(dims), "nodes": N, "dof": N * 26,
+                     "primal_MLUPS": prim, "adjoint_MLUPS": adj, "adjoint_over_primal_time": prim / adj,
+                     "solve_MLUPS": 2.0 * N * nsteps * args.steps / wall / 1e6,
+                     "paper_m2090_primal_MLUPS": p_mlups, "paper_m2090_adjoint_MLUPS": a_mlups})
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"metric": "primal and adjoint MLUPS on the paper's scaling meshes",
+                      "workload": "meshes", "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "primal_steps": nsteps, "dtype": "f32",
+                      "data": "synthetic", "rows": rows}), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """A few launches of each kernel on a lattice that still exceeds L2."""
     import torch
@@ -446,12 +582,14 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="mixer3d",
-                    choices=["mixer3d", "exchanger3d", "batch64", "serve"])
+                    choices=["mixer3d", "exchanger3d", "batch64", "serve", "oneshot", "meshes"])
     ap.add_argument("--count", type=int, default=0, help="instances (batch64) or requests (serve)")
     ap.add_argument("--size-scale", type=float, default=1.0, help="batch64: linear size factor")
     ap.add_argument("--rates", default="2,20,200", help="serve: arrival rates per second")
     ap.add_argument("--max-nodes", type=float, default=3e7, help="serve: largest request")
     ap.add_argument("--tick", type=int, default=200, help="serve: most steps per request per tick")
+    ap.add_argument("--oneshot-iters", type=int, default=200,
+                    help="oneshot: one-shot iterations per timed step")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the small ncu case instead: mixer3d physics on 256x128x64, "
                          "6 primal + 6 adjoint steps, objective over the last 2 "
@@ -463,6 +601,10 @@ def main(argv=None):
         return run_batch64(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "oneshot":
+        return run_oneshot(args)
+    if args.workload == "meshes":
+        return run_meshes(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -223,7 +223,7 @@ lbm_status lbm_profile_read(lbm_handle h, double* out);
 /* Primal steps recomputed by the checkpoint schedule since the last reset. */
 long long lbm_recompute_steps(lbm_handle h);
 
-/* Batched primal steps (SURVEY K7 / continuous batching): advance each of
+/* Batched primal steps (continuous batching): advance each of
  * the n handles by up to k steps, one kernel launch per step covering every
  * handle that has not reached its horizon (at most 64 handles per launch;
  * larger batches are split).  The per-node arithmetic is that of
@@ -239,6 +239,66 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k);
  * handle whose adjoint has not started starts at its current primal time.
  * Same requirements and errors as lbm_batch_primal_step. */
 lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k);
+
+/* ---- one-shot optimisation (Sec. 3.3) -------------------------------------
+ * The design theta is optimised together with the flow.  One iteration:
+ *   1. one primal step f^{k+1} = S W(f^k, theta^k)        (Eq. normal:iteration)
+ *   2. one ALBS step at the current primal state, with the objective source
+ *      every iteration: v^{k+1} = (d(SW)/df(f^k))^T v^k + dF/df(f^k)
+ *                                                        (Eq. adjoint:iteration)
+ *   3. the gradient estimate g^k = (d(SW)/dtheta(f^k))^T v^k from the adjoint
+ *      iterate step 2 consumes                           (Eq. adjoint:derivative)
+ *   4. on design nodes, the update of Eq. gradient:update on the penalised
+ *      objective s J - penalty P, with P = sum theta (1 - theta) of Eq. P:
+ *        theta <- min(max(theta + zeta (s g - penalty (1 - 2 theta)), 0), 1)
+ *      s = +1 when J is maximised, -1 when it is minimised; evaluated in
+ *      FP64, stored in FP32.
+ * The objective is F of the current state: the horizon and time weights of
+ * lbm_params do not apply.  theta is the handle's own array (lbm_set_theta
+ * sets the starting design; a one-shot run changes it in place).  While a
+ * one-shot run is active the current state is the state of time 0 for
+ * lbm_get_populations, lbm_set_populations (which replaces f^k),
+ * lbm_adjoint_seed (which replaces v^k), lbm_get_adjoint (v^k) and
+ * lbm_gradient (the last estimate g); lbm_primal_step, lbm_adjoint_step and
+ * the batched steps return LBM_ERR_STATE until lbm_reset or lbm_set_theta. */
+
+/* Design mask: N bytes (host or device, copied); nonzero marks a node whose
+ * theta the one-shot update may change.  NULL restores the default: every
+ * FLUID node.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+lbm_status lbm_set_design(lbm_handle h, const uint8_t* mask);
+
+/* Start a one-shot run: f^0 = rest state, v^0 = 0, g = 0 (asynchronous). */
+lbm_status lbm_oneshot_reset(lbm_handle h);
+
+/* iters one-shot iterations, asynchronous on the handle's stream: per
+ * iteration one primal launch, one adjoint launch, one update launch (and,
+ * for the outlet-variance objective, the fold of the outlet mean the
+ * adjoint source needs).  zeta >= 0 and penalty >= 0 are finite; maximize:
+ * nonzero ascends J, zero descends.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (no
+ * one-shot run started), LBM_ERR_OOM (the pool cannot hold two states). */
+lbm_status lbm_oneshot_step(lbm_handle h, int iters, double zeta, double penalty, int maximize);
+
+/* F(f^k) of the current one-shot state and the penalty P over the design
+ * nodes, into host doubles (either may be NULL); synchronises.  The sums
+ * are taken per block and folded in a fixed order (reproducible). */
+lbm_status lbm_oneshot_eval(lbm_handle h, double* J, double* P);
+
+/* Threshold scan of Sec. 3.2.  For each level eta[i] the design nodes are
+ * set solid (theta = 1) where w = 1 - theta < eta[i], both in FP32, and
+ * fluid (theta = 0) otherwise; the primal runs nsteps >= 1 steps from rest
+ * on that design and J_out[i] = F(f^nsteps).  The continuous theta is
+ * restored afterwards and the handle is reset (any one-shot or unsteady run
+ * ends).  eta and J_out: host arrays of n >= 1 doubles; synchronises.
+ * Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_threshold_scan(lbm_handle h, const double* eta, int n, int nsteps, double* J_out);
+
+/* Binarise the handle's theta in place with one level eta (the rule of
+ * lbm_threshold_scan) and reset the handle.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+lbm_status lbm_threshold_apply(lbm_handle h, double eta);
+
+/* Copy the handle's current theta (N floats) into dst (host or device);
+ * synchronises when dst is host memory. */
+lbm_status lbm_get_theta(lbm_handle h, float* dst);
 
 /* Objective F(f) of one pre-collision state, evaluated without allocating
  * any device memory.  The paper has no counterpart: this entry point exists

@@ -35,7 +35,9 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_theta", "lbm_
            "lbm_get_populations", "lbm_get_populations_at", "lbm_set_populations", "lbm_get_adjoint", "lbm_get_flags",
            "lbm_check_finite", "lbm_sizes", "lbm_last_timing", "lbm_profile",
            "lbm_profile_read", "lbm_recompute_steps", "lbm_batch_primal_step",
-           "lbm_batch_adjoint_step", "lbm_state_objective_noalloc",
+           "lbm_batch_adjoint_step", "lbm_set_design", "lbm_oneshot_reset",
+           "lbm_oneshot_step", "lbm_oneshot_eval", "lbm_threshold_scan",
+           "lbm_threshold_apply", "lbm_get_theta", "lbm_state_objective_noalloc",
            "lbm_noalloc_last_error"]
 
 
@@ -98,6 +100,13 @@ def lib():
         L.lbm_recompute_steps.restype = C.c_longlong
         L.lbm_batch_primal_step.argtypes = [C.POINTER(vp), i, i]
         L.lbm_batch_adjoint_step.argtypes = [C.POINTER(vp), i, i]
+        L.lbm_set_design.argtypes = [vp, vp]
+        L.lbm_oneshot_reset.argtypes = [vp]
+        L.lbm_oneshot_step.argtypes = [vp, i, d, d, i]
+        L.lbm_oneshot_eval.argtypes = [vp, C.POINTER(d), C.POINTER(d)]
+        L.lbm_threshold_scan.argtypes = [vp, C.POINTER(d), i, i, C.POINTER(d)]
+        L.lbm_threshold_apply.argtypes = [vp, d]
+        L.lbm_get_theta.argtypes = [vp, vp]
         L.lbm_state_objective_noalloc.argtypes = [C.POINTER(LbmParams), vp, vp, vp, vp,
                                                   C.POINTER(d)]
         L.lbm_noalloc_last_error.argtypes = []
@@ -339,6 +348,53 @@ class Solver:
 
     def recompute_steps(self) -> int:
         return int(self._L.lbm_recompute_steps(self._h))
+
+    # ---- one-shot optimisation (Sec. 3.3) and threshold (Sec. 3.2) ---------------
+    def set_design(self, mask=None):
+        """Design mask (N values, nonzero = updated) or None for the FLUID nodes."""
+        import torch
+        if mask is None:
+            self._check(self._L.lbm_set_design(self._h, None))
+            return
+        if isinstance(mask, torch.Tensor):
+            m = mask.detach().to(torch.uint8).contiguous().reshape(-1)
+            self._keep_mask = m
+            self._sync_in()
+        else:
+            m = np.ascontiguousarray(np.asarray(mask).reshape(-1).astype(np.uint8))
+        self._check(self._L.lbm_set_design(self._h, _ptr(m)))
+
+    def oneshot_reset(self):
+        self._check(self._L.lbm_oneshot_reset(self._h))
+
+    def oneshot_step(self, iters: int, zeta: float, penalty: float = 0.0, maximize: bool = True):
+        self._check(self._L.lbm_oneshot_step(self._h, int(iters), float(zeta), float(penalty),
+                                             1 if maximize else 0))
+
+    def oneshot_eval(self):
+        """(J of the current state, penalty P over the design nodes)."""
+        J, P = C.c_double(), C.c_double()
+        self._check(self._L.lbm_oneshot_eval(self._h, C.byref(J), C.byref(P)))
+        return J.value, P.value
+
+    def threshold_scan(self, etas, nsteps: int):
+        e = (C.c_double * len(etas))(*[float(v) for v in etas])
+        out = (C.c_double * len(etas))()
+        self._check(self._L.lbm_threshold_scan(self._h, e, len(etas), int(nsteps), out))
+        return list(out)
+
+    def threshold_apply(self, eta: float):
+        self._check(self._L.lbm_threshold_apply(self._h, float(eta)))
+
+    def theta(self, out=None):
+        """The handle's current theta (N float32) into ``out`` or a new device tensor."""
+        import torch
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.float32, device="cuda")
+        self._sync_in()
+        self._check(self._L.lbm_get_theta(self._h, _ptr(out)))
+        self._sync_out()
+        return out
 
 
 def state_objective_noalloc(P: Problem, f, theta, flags, stream=None) -> float:

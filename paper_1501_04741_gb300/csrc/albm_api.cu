@@ -73,6 +73,12 @@ struct lbm_ctx {
   bool primal_timed = false, adjoint_timed = false;
   long long recompute_steps = 0;
   long long launches_other = 0;     // objective / fold / import / export kernels
+  // one-shot optimisation: the current state is the pool buffer labelled 0
+  bool oneshot = false;
+  uint8_t* design = nullptr;        // design mask (device, N); null until first use
+  bool design_default = true;       // mask = FLUID nodes
+  double* os_stats = nullptr;       // objective record of the current state (2 doubles)
+  float* theta_saved = nullptr;     // continuous design during a threshold scan
   std::string err;
 };
 
@@ -253,6 +259,55 @@ __global__ void __launch_bounds__(1024) fold_partials_kernel(const double* __res
     out[1] = sh[1][0];
   }
 }
+
+// ---- one-shot optimisation (Sec. 3.3) --------------------------------------
+// Eq. gradient:update with the penalty of Eq. P on design nodes, in FP64:
+// theta <- clamp(theta + zeta (s g - penalty (1 - 2 theta)), 0, 1)
+__global__ void __launch_bounds__(256) oneshot_update_kernel(long long N, float* __restrict__ theta,
+                                                             const double* __restrict__ grad,
+                                                             const uint8_t* __restrict__ design,
+                                                             double zeta, double penalty,
+                                                             double s) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N || !design[i]) return;
+  const double t = (double)theta[i];
+  const double d = s * grad[i] - penalty * (1.0 - 2.0 * t);
+  double tn = t + zeta * d;
+  tn = tn < 0.0 ? 0.0 : (tn > 1.0 ? 1.0 : tn);
+  theta[i] = (float)tn;
+}
+
+// per-block sums of theta (1 - theta) over design nodes (P of Eq. P)
+__global__ void __launch_bounds__(256) penalty_kernel(long long N, const float* __restrict__ theta,
+                                                      const uint8_t* __restrict__ design,
+                                                      double* __restrict__ partials) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (i < N && design[i]) {
+    const double t = (double)theta[i];
+    v = t * (1.0 - t);
+  }
+  block_partial2(v, 0.0, partials + 2 * (long long)blockIdx.x);
+}
+
+// threshold of Sec. 3.2: w = 1 - theta below eta -> solid (theta = 1), else
+// fluid (theta = 0), in FP32, on design nodes; other nodes copied
+__global__ void __launch_bounds__(256) threshold_kernel(long long N, const float* __restrict__ src,
+                                                        float* __restrict__ dst,
+                                                        const uint8_t* __restrict__ design,
+                                                        float eta) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float t = src[i];
+  dst[i] = design[i] ? ((1.0f - t < eta) ? 1.0f : 0.0f) : t;
+}
+
+// default design mask: FLUID nodes
+__global__ void __launch_bounds__(256) fluid_mask_kernel(long long N, const uint8_t* __restrict__ flags,
+                                                         uint8_t* __restrict__ design) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) design[i] = flags[i] == FLUID ? 1 : 0;
+}
 }  // namespace albm
 
 // after a synchronisation: report an expired bounded wait of a staged kernel
@@ -390,6 +445,7 @@ static lbm_status launch_adjoint(lbm_ctx* h, int n, int has_next) {
 }
 
 static lbm_status do_reset(lbm_ctx* h) {
+  h->oneshot = false;
   for (auto& t : h->buf_time) t = -1;
   int b;
   lbm_status s = acquire(h, &b);
@@ -600,6 +656,9 @@ void lbm_destroy(lbm_handle h) {
   cudaFree(h->counter);
   cudaFree(h->lam[0]);
   cudaFree(h->lam[1]);
+  cudaFree(h->design);
+  cudaFree(h->os_stats);
+  cudaFree(h->theta_saved);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->t0) cudaEventDestroy(h->t0);
   if (h->t1) cudaEventDestroy(h->t1);
@@ -628,6 +687,7 @@ lbm_status lbm_primal_step(lbm_handle h, int k) {
   if (k < 0 || h->t + k > h->p.nsteps)
     FAIL(h, LBM_ERR_ARG, "primal steps %d from time %d exceed the horizon %d", k, h->t,
          h->p.nsteps);
+  if (h->oneshot) FAIL(h, LBM_ERR_STATE, "a one-shot run is active; reset first");
   if (h->t_adj >= 0) FAIL(h, LBM_ERR_STATE, "the adjoint of this trajectory has started; reset first");
   CK(h, cudaEventRecord(h->t0, h->stream));
   for (int i = 0; i < k; ++i) {
@@ -693,6 +753,7 @@ static lbm_status adjoint_start(lbm_handle h) {
 lbm_status lbm_adjoint_step(lbm_handle h, int k) {
   if (!h) return LBM_ERR_ARG;
   if (k < 0) FAIL(h, LBM_ERR_ARG, "negative step count");
+  if (h->oneshot) FAIL(h, LBM_ERR_STATE, "a one-shot run is active; reset first");
   CK(h, cudaEventRecord(h->t2, h->stream));
   if (h->t_adj < 0) {
     lbm_status s = adjoint_start(h);
@@ -764,6 +825,10 @@ static lbm_status batch_check(const lbm_handle* hs, int n) {
   if (!hs || n < 1) return LBM_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     if (!hs[i]) return LBM_ERR_ARG;
+    if (hs[i]->oneshot) {
+      hs[0]->err = "a batched handle has an active one-shot run";
+      return LBM_ERR_STATE;
+    }
     if (hs[i]->ks.primal != hs[0]->ks.primal || hs[i]->stream != hs[0]->stream) {
       hs[0]->err = "batched handles need the same lattice, collision, scalars, precision and stream";
       return LBM_ERR_ARG;
@@ -979,7 +1044,7 @@ lbm_status lbm_set_populations(lbm_handle h, const float* src) {
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "import: %s", cudaGetErrorString(e));
   h->buf_time[b] = 0;
   h->t = 0;
-  h->t_adj = -1;
+  h->t_adj = h->oneshot ? 0 : -1;
   CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * 2 * (size_t)(h->p.nsteps + 1), h->stream));
   return LBM_OK;
 }
@@ -1040,6 +1105,256 @@ lbm_status lbm_last_timing(lbm_handle h, float* primal_ms, float* adjoint_ms) {
     *adjoint_ms = 0.f;
     if (h->adjoint_timed) CK(h, cudaEventElapsedTime(adjoint_ms, h->t2, h->t3));
   }
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// one-shot optimisation (Sec. 3.3) and the threshold scan (Sec. 3.2)
+// ---------------------------------------------------------------------------
+static unsigned node_blocks(const lbm_ctx* h) { return (unsigned)((h->N + 255) / 256); }
+
+static lbm_status ensure_design(lbm_ctx* h) {
+  if (!h->design) {
+    CK(h, cudaMalloc(&h->design, (size_t)h->N));
+    h->design_default = true;
+  }
+  if (h->design_default) {
+    albm::fluid_mask_kernel<<<node_blocks(h), 256, 0, h->stream>>>(h->N, h->flags, h->design);
+    h->launches_other++;
+    CK(h, cudaGetLastError());
+  }
+  if (!h->os_stats) CK(h, cudaMalloc(&h->os_stats, 2 * sizeof(double)));
+  return LBM_OK;
+}
+
+static int oneshot_buf(lbm_ctx* h) { return find_buf(h, 0); }
+
+// F of the state in buffer b into h->os_stats (objective kernel + fold)
+static lbm_status state_objective(lbm_ctx* h, int b) {
+  StepArgs a = blank_args(h);
+  a.Bin = h->bufs[b];
+  a.obj = h->partials;
+  cudaError_t e = h->ks.objective(h->kp, a, h->stream);
+  h->launches_other++;
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "objective kernel launch: %s", cudaGetErrorString(e));
+  albm::fold_partials_kernel<<<1, 1024, 0, h->stream>>>(h->partials, h->nblocks, h->os_stats);
+  h->launches_other++;
+  CK(h, cudaGetLastError());
+  return LBM_OK;
+}
+
+// the objective from its two folded sums (the formulas of lbm_objective)
+static double objective_value(const lbm_ctx* h, const double* st) {
+  const double A = h->n_out > 0 ? (double)h->n_out : 1.0;
+  switch (h->p.objective) {
+    case LBM_OBJ_VARIANCE: {
+      const double m = st[0] / A;
+      return st[1] / A - m * m;
+    }
+    case LBM_OBJ_HEATFLUX_DP:
+      return st[0] + 0.1 * h->p.rho_out / 3.0;
+    default:
+      return st[0];
+  }
+}
+
+static lbm_status oneshot_iteration(lbm_ctx* h, double zeta, double penalty, double s) {
+  const int src = oneshot_buf(h);
+  if (src < 0) FAIL(h, LBM_ERR_STATE, "the one-shot state is not held");
+  int dst;
+  lbm_status st = acquire(h, &dst);
+  if (st) return st;
+  const bool variance = h->p.objective == LBM_OBJ_VARIANCE;
+  // 1. primal step f^k -> f^{k+1}; the variance source needs the outlet mean of f^k
+  StepArgs a = blank_args(h);
+  a.Bin = h->bufs[src];
+  a.Bout = h->bufs[dst];
+  a.obj = variance ? h->partials : nullptr;
+  a.err = h->d_err;
+  int slot;
+  prof_begin(h, K_PRIMAL, &slot);
+  cudaError_t e = h->staged == 2   ? h->ks.primal_tiles(h->kp, a, h->stream)
+                  : h->staged == 3 ? h->ks.primal_async(h->kp, a, h->stream)
+                                   : h->ks.primal(h->kp, a, h->stream);
+  prof_end(h, slot);
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "primal kernel launch: %s", cudaGetErrorString(e));
+  if (variance) {
+    albm::fold_partials_kernel<<<1, 1024, 0, h->stream>>>(
+        h->partials, h->staged ? h->ntiles : h->ks.primal_partials(h->kp), h->os_stats);
+    h->launches_other++;
+    CK(h, cudaGetLastError());
+  }
+  // 2.-3. ALBS step at f^k with the source every iteration; the adjoint
+  // kernel adds the estimate g^k to the (cleared) gradient
+  CK(h, cudaMemsetAsync(h->grad, 0, sizeof(double) * (size_t)h->N, h->stream));
+  StepArgs b = blank_args(h);
+  b.Bin = h->bufs[src];
+  b.lam_in = h->lam[h->lam_cur];
+  b.lam_out = h->lam[1 - h->lam_cur];
+  b.grad = h->grad;
+  b.ws = 1.0f;
+  b.stat_n = variance ? h->os_stats : nullptr;
+  b.has_next = 1;
+  b.err = h->d_err;
+  prof_begin(h, K_ADJOINT, &slot);
+  e = h->staged == 2   ? h->ks.adjoint_tiles(h->kp, b, h->stream)
+      : h->staged == 3 ? h->ks.adjoint_async(h->kp, b, h->stream)
+                       : h->ks.adjoint(h->kp, b, h->stream);
+  prof_end(h, slot);
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "adjoint kernel launch: %s", cudaGetErrorString(e));
+  h->lam_cur = 1 - h->lam_cur;
+  // 4. design update
+  albm::oneshot_update_kernel<<<node_blocks(h), 256, 0, h->stream>>>(h->N, h->theta, h->grad,
+                                                                     h->design, zeta, penalty, s);
+  h->launches_other++;
+  CK(h, cudaGetLastError());
+  h->buf_time[src] = -1;
+  h->buf_time[dst] = 0;
+  return LBM_OK;
+}
+
+extern "C" {
+
+lbm_status lbm_set_design(lbm_handle h, const uint8_t* mask) {
+  if (!h) return LBM_ERR_ARG;
+  if (!h->design) CK(h, cudaMalloc(&h->design, (size_t)h->N));
+  if (!mask) {
+    h->design_default = true;
+    return ensure_design(h);
+  }
+  h->design_default = false;
+  CK(h, cudaMemcpyAsync(h->design, mask, (size_t)h->N, cudaMemcpyDefault, h->stream));
+  if (!is_device_ptr(mask)) CK(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_oneshot_reset(lbm_handle h) {
+  if (!h) return LBM_ERR_ARG;
+  lbm_status s = do_reset(h);   // f^0 = rest state in the buffer of time 0
+  if (s) return s;
+  s = ensure_design(h);
+  if (s) return s;
+  CK(h, cudaMemsetAsync(h->lam[0], 0, sizeof(float) * (size_t)h->M * (size_t)h->N, h->stream));
+  CK(h, cudaMemsetAsync(h->grad, 0, sizeof(double) * (size_t)h->N, h->stream));
+  CK(h, cudaMemsetAsync(h->os_stats, 0, 2 * sizeof(double), h->stream));
+  h->lam_cur = 0;
+  h->t_adj = 0;
+  h->oneshot = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_oneshot_step(lbm_handle h, int iters, double zeta, double penalty, int maximize) {
+  if (!h) return LBM_ERR_ARG;
+  if (!h->oneshot) FAIL(h, LBM_ERR_STATE, "no one-shot run started (lbm_oneshot_reset)");
+  if (iters < 0 || !(zeta >= 0.0) || !(penalty >= 0.0) || !std::isfinite(zeta) ||
+      !std::isfinite(penalty))
+    FAIL(h, LBM_ERR_ARG, "one-shot needs iters >= 0 and finite zeta, penalty >= 0");
+  const double s = maximize ? 1.0 : -1.0;
+  for (int i = 0; i < iters; ++i) {
+    lbm_status st = oneshot_iteration(h, zeta, penalty, s);
+    if (st) return st;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_oneshot_eval(lbm_handle h, double* J, double* P) {
+  if (!h) return LBM_ERR_ARG;
+  if (!h->oneshot) FAIL(h, LBM_ERR_STATE, "no one-shot run started (lbm_oneshot_reset)");
+  double st[2] = {0.0, 0.0}, pp[2] = {0.0, 0.0};
+  if (J) {
+    lbm_status s = state_objective(h, oneshot_buf(h));
+    if (s) return s;
+    CK(h, cudaMemcpyAsync(st, h->os_stats, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));   // os_stats is reused below
+  }
+  if (P) {
+    albm::penalty_kernel<<<node_blocks(h), 256, 0, h->stream>>>(h->N, h->theta, h->design,
+                                                               h->partials);
+    albm::fold_partials_kernel<<<1, 1024, 0, h->stream>>>(h->partials, (long long)node_blocks(h),
+                                                          h->os_stats);
+    h->launches_other += 2;
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(pp, h->os_stats, sizeof(pp), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  {
+    lbm_status ts = check_timeout(h);
+    if (ts) return ts;
+  }
+  if (J) *J = objective_value(h, st);
+  if (P) *P = pp[0];
+  return LBM_OK;
+}
+
+lbm_status lbm_threshold_scan(lbm_handle h, const double* eta, int n, int nsteps, double* J_out) {
+  if (!h || !eta || !J_out || n < 1 || nsteps < 1) return LBM_ERR_ARG;
+  lbm_status s = ensure_design(h);
+  if (s) return s;
+  if (!h->theta_saved) CK(h, cudaMalloc(&h->theta_saved, sizeof(float) * (size_t)h->N));
+  CK(h, cudaMemcpyAsync(h->theta_saved, h->theta, sizeof(float) * (size_t)h->N,
+                        cudaMemcpyDeviceToDevice, h->stream));
+  lbm_status result = LBM_OK;
+  for (int i = 0; i < n && result == LBM_OK; ++i) {
+    albm::threshold_kernel<<<node_blocks(h), 256, 0, h->stream>>>(h->N, h->theta_saved, h->theta,
+                                                                 h->design, (float)eta[i]);
+    h->launches_other++;
+    if (cudaGetLastError() != cudaSuccess) {
+      h->err = "threshold kernel launch failed";
+      result = LBM_ERR_CUDA;
+      break;
+    }
+    result = do_reset(h);
+    int cur = find_buf(h, 0);
+    for (int k = 0; k < nsteps && result == LBM_OK; ++k) {
+      int dst;
+      result = acquire(h, &dst);
+      if (result) break;
+      result = launch_primal(h, cur, dst, 0, false, K_PRIMAL);
+      h->buf_time[cur] = -1;
+      h->buf_time[dst] = 0;
+      cur = dst;
+    }
+    if (result == LBM_OK) result = state_objective(h, cur);
+    double st[2] = {0.0, 0.0};
+    if (result == LBM_OK) {
+      if (cudaMemcpyAsync(st, h->os_stats, sizeof(st), cudaMemcpyDeviceToHost, h->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        h->err = "threshold scan: reading the objective failed";
+        result = LBM_ERR_CUDA;
+      } else {
+        result = check_timeout(h);
+      }
+    }
+    if (result == LBM_OK) J_out[i] = objective_value(h, st);
+  }
+  // restore the continuous design and a fresh state whatever happened
+  cudaMemcpyAsync(h->theta, h->theta_saved, sizeof(float) * (size_t)h->N, cudaMemcpyDeviceToDevice,
+                  h->stream);
+  lbm_status r2 = do_reset(h);
+  return result ? result : r2;
+}
+
+lbm_status lbm_threshold_apply(lbm_handle h, double eta) {
+  if (!h || !std::isfinite(eta)) return LBM_ERR_ARG;
+  lbm_status s = ensure_design(h);
+  if (s) return s;
+  if (!h->theta_saved) CK(h, cudaMalloc(&h->theta_saved, sizeof(float) * (size_t)h->N));
+  CK(h, cudaMemcpyAsync(h->theta_saved, h->theta, sizeof(float) * (size_t)h->N,
+                        cudaMemcpyDeviceToDevice, h->stream));
+  albm::threshold_kernel<<<node_blocks(h), 256, 0, h->stream>>>(h->N, h->theta_saved, h->theta,
+                                                               h->design, (float)eta);
+  h->launches_other++;
+  CK(h, cudaGetLastError());
+  return do_reset(h);
+}
+
+lbm_status lbm_get_theta(lbm_handle h, float* dst) {
+  if (!h || !dst) return LBM_ERR_ARG;
+  CK(h, cudaMemcpyAsync(dst, h->theta, sizeof(float) * (size_t)h->N, cudaMemcpyDefault, h->stream));
+  if (!is_device_ptr(dst)) CK(h, cudaStreamSynchronize(h->stream));
   return LBM_OK;
 }
 
