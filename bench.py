@@ -460,7 +460,9 @@ def run_oneshot(args):
     peak, peak_kind = _peaks()
     storage = {"fp32": 4, "bf16": 2, "fp16": 2}[P.precision]
     bp = bytes_per_node(s.M, storage, "primal")
-    ba = bytes_per_node(s.M, storage, "adjoint")
+    # one-shot adjoint: lambda in/out and f as in the unsteady step, theta and
+    # flag read, design mask read, theta written, gradient estimate written
+    ba = s.M * 4 * 2 + s.M * storage + 4 + 1 + 1 + 4 + 8
     (n_p, ms_p), (n_a, ms_a) = prof["primal"], prof["adjoint"]
     prim_ms, adj_ms = ms_p / max(n_p, 1), ms_a / max(n_a, 1)
     adj_gbs = ba * N / (adj_ms / 1e3) / 1e9

@@ -251,8 +251,8 @@ lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k);
  *   4. on design nodes, the update of Eq. gradient:update on the penalised
  *      objective s J - penalty P, with P = sum theta (1 - theta) of Eq. P:
  *        theta <- min(max(theta + zeta (s g - penalty (1 - 2 theta)), 0), 1)
- *      s = +1 when J is maximised, -1 when it is minimised; evaluated in
- *      FP64, stored in FP32.
+ *      s = +1 when J is maximised, -1 when it is minimised; evaluated and
+ *      stored in FP32 (zeta and penalty are rounded to FP32).
  * The objective is F of the current state: the horizon and time weights of
  * lbm_params do not apply.  theta is the handle's own array (lbm_set_theta
  * sets the starting design; a one-shot run changes it in place).  While a
@@ -271,9 +271,10 @@ lbm_status lbm_set_design(lbm_handle h, const uint8_t* mask);
 lbm_status lbm_oneshot_reset(lbm_handle h);
 
 /* iters one-shot iterations, asynchronous on the handle's stream: per
- * iteration one primal launch, one adjoint launch, one update launch (and,
- * for the outlet-variance objective, the fold of the outlet mean the
- * adjoint source needs).  zeta >= 0 and penalty >= 0 are finite; maximize:
+ * iteration one primal launch and one adjoint launch that also writes g and
+ * updates theta (and, for the outlet-variance objective, the fold of the
+ * outlet mean the adjoint source needs).  The iteration always runs the
+ * one-thread-per-node kernels, whatever lbm_params.kernel selects.  zeta >= 0 and penalty >= 0 are finite; maximize:
  * nonzero ascends J, zero descends.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (no
  * one-shot run started), LBM_ERR_OOM (the pool cannot hold two states). */
 lbm_status lbm_oneshot_step(lbm_handle h, int iters, double zeta, double penalty, int maximize);

@@ -261,22 +261,6 @@ __global__ void __launch_bounds__(1024) fold_partials_kernel(const double* __res
 }
 
 // ---- one-shot optimisation (Sec. 3.3) --------------------------------------
-// Eq. gradient:update with the penalty of Eq. P on design nodes, in FP64:
-// theta <- clamp(theta + zeta (s g - penalty (1 - 2 theta)), 0, 1)
-__global__ void __launch_bounds__(256) oneshot_update_kernel(long long N, float* __restrict__ theta,
-                                                             const double* __restrict__ grad,
-                                                             const uint8_t* __restrict__ design,
-                                                             double zeta, double penalty,
-                                                             double s) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N || !design[i]) return;
-  const double t = (double)theta[i];
-  const double d = s * grad[i] - penalty * (1.0 - 2.0 * t);
-  double tn = t + zeta * d;
-  tn = tn < 0.0 ? 0.0 : (tn > 1.0 ? 1.0 : tn);
-  theta[i] = (float)tn;
-}
-
 // per-block sums of theta (1 - theta) over design nodes (P of Eq. P)
 __global__ void __launch_bounds__(256) penalty_kernel(long long N, const float* __restrict__ theta,
                                                       const uint8_t* __restrict__ design,
@@ -1175,20 +1159,17 @@ static lbm_status oneshot_iteration(lbm_ctx* h, double zeta, double penalty, dou
   a.err = h->d_err;
   int slot;
   prof_begin(h, K_PRIMAL, &slot);
-  cudaError_t e = h->staged == 2   ? h->ks.primal_tiles(h->kp, a, h->stream)
-                  : h->staged == 3 ? h->ks.primal_async(h->kp, a, h->stream)
-                                   : h->ks.primal(h->kp, a, h->stream);
+  cudaError_t e = h->ks.primal(h->kp, a, h->stream);
   prof_end(h, slot);
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "primal kernel launch: %s", cudaGetErrorString(e));
   if (variance) {
-    albm::fold_partials_kernel<<<1, 1024, 0, h->stream>>>(
-        h->partials, h->staged ? h->ntiles : h->ks.primal_partials(h->kp), h->os_stats);
+    albm::fold_partials_kernel<<<1, 1024, 0, h->stream>>>(h->partials, h->ks.primal_partials(h->kp),
+                                                          h->os_stats);
     h->launches_other++;
     CK(h, cudaGetLastError());
   }
-  // 2.-3. ALBS step at f^k with the source every iteration; the adjoint
-  // kernel adds the estimate g^k to the (cleared) gradient
-  CK(h, cudaMemsetAsync(h->grad, 0, sizeof(double) * (size_t)h->N, h->stream));
+  // 2.-4. ALBS step at f^k with the source every iteration; the adjoint
+  // kernel writes the estimate g^k into grad and updates theta in place
   StepArgs b = blank_args(h);
   b.Bin = h->bufs[src];
   b.lam_in = h->lam[h->lam_cur];
@@ -1198,18 +1179,16 @@ static lbm_status oneshot_iteration(lbm_ctx* h, double zeta, double penalty, dou
   b.stat_n = variance ? h->os_stats : nullptr;
   b.has_next = 1;
   b.err = h->d_err;
+  b.os.design = h->design;
+  b.os.theta_out = h->theta;
+  b.os.zeta = (float)zeta;
+  b.os.penalty = (float)penalty;
+  b.os.sign = (float)s;
   prof_begin(h, K_ADJOINT, &slot);
-  e = h->staged == 2   ? h->ks.adjoint_tiles(h->kp, b, h->stream)
-      : h->staged == 3 ? h->ks.adjoint_async(h->kp, b, h->stream)
-                       : h->ks.adjoint(h->kp, b, h->stream);
+  e = h->ks.adjoint(h->kp, b, h->stream);
   prof_end(h, slot);
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "adjoint kernel launch: %s", cudaGetErrorString(e));
   h->lam_cur = 1 - h->lam_cur;
-  // 4. design update
-  albm::oneshot_update_kernel<<<node_blocks(h), 256, 0, h->stream>>>(h->N, h->theta, h->grad,
-                                                                     h->design, zeta, penalty, s);
-  h->launches_other++;
-  CK(h, cudaGetLastError());
   h->buf_time[src] = -1;
   h->buf_time[dst] = 0;
   return LBM_OK;

@@ -169,9 +169,10 @@ struct Gather {
 // ---------------------------------------------------------------------------
 // primal step: B^{n+1}(x) = W^x(f^n(x)); optional objective terms of f^n
 // ---------------------------------------------------------------------------
-// OBJ = false: the step records no objective (obj is null); the objective
-// terms and the block reduction are compiled out.
-template <class L, int NS, bool MRT, class S, bool OBJ = true>
+// OBJ: objective form compiled in (obj_kind); 0 when the step records no
+// objective (obj is null): the objective terms and the block reduction are
+// compiled out.
+template <class L, int NS, bool MRT, class S, int OBJ = 2>
 __device__ __forceinline__ void primal_body(const KParams& P, const S* __restrict__ Bin,
                                             S* __restrict__ Bout, const float* __restrict__ theta,
                                             const uint8_t* __restrict__ flags,
@@ -185,7 +186,7 @@ __device__ __forceinline__ void primal_body(const KParams& P, const S* __restric
     Gather<L, NS, S>::pre(geo, P.N, Bin, d, g);
     const uint8_t type = flags[idx];
     const float th = theta[idx];
-    Ops::forward(P, type, th, geo.y, d, g, OBJ && obj != nullptr, o1, o2);
+    Ops::template forward<OBJ>(P, type, th, geo.y, d, g, OBJ != 0 && obj != nullptr, o1, o2);
 #pragma unroll
     for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, d[i]);
 #pragma unroll
@@ -193,12 +194,12 @@ __device__ __forceinline__ void primal_body(const KParams& P, const S* __restric
 #pragma unroll
       for (int i = 0; i < QS; ++i) st(Bout + (long long)(Q + s * QS + i) * P.N + idx, g[s][i]);
   }
-  if (OBJ && obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
+  if (OBJ != 0 && obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
 }
 
-template <class L, int NS, bool MRT, class S, bool OBJ>
+template <class L, int NS, bool MRT, class S, int OBJ>
 __global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK,
-                                  OBJ ? ALBM_PRIMAL_MINB
+                                  OBJ != 0 ? ALBM_PRIMAL_MINB
                                       : (NS >= 2 ? ALBM_PRIMAL_MINB_NOOBJ_NS2 : ALBM_PRIMAL_MINB_NOOBJ))
     primal_kernel(KParams P, const S* __restrict__ Bin,
                                                      S* __restrict__ Bout,
@@ -256,7 +257,7 @@ __device__ __forceinline__ void gather_pair(const S* rowp, int ex, int x, int nx
   }
 }
 
-template <class L, int NS, bool MRT, class S, bool OBJ = true>
+template <class L, int NS, bool MRT, class S, int OBJ = 2>
 __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __restrict__ Bin,
                                                  S* __restrict__ Bout, const float* __restrict__ theta,
                                                  const uint8_t* __restrict__ flags,
@@ -291,8 +292,8 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
     const long long idx = row * P.nx + x;
     const float2 th = *reinterpret_cast<const float2*>(theta + idx);
     const uint8_t ta = flags[idx], tb = flags[idx + 1];
-    Ops::forward(P, ta, th.x, y, da, ga, OBJ && obj != nullptr, o1, o2);
-    Ops::forward(P, tb, th.y, y, db, gb, OBJ && obj != nullptr, o1, o2);
+    Ops::template forward<OBJ>(P, ta, th.x, y, da, ga, OBJ != 0 && obj != nullptr, o1, o2);
+    Ops::template forward<OBJ>(P, tb, th.y, y, db, gb, OBJ != 0 && obj != nullptr, o1, o2);
 #pragma unroll
     for (int i = 0; i < Q; ++i) Pair<S>::st(Bout + (long long)i * P.N + idx, da[i], db[i]);
 #pragma unroll
@@ -301,10 +302,10 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
       for (int i = 0; i < QS; ++i)
         Pair<S>::st(Bout + (long long)(Q + s * QS + i) * P.N + idx, ga[s][i], gb[s][i]);
   }
-  if (OBJ && obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
+  if (OBJ != 0 && obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
 }
 
-template <class L, int NS, bool MRT, class S, bool OBJ>
+template <class L, int NS, bool MRT, class S, int OBJ>
 __global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK, 4) primal_pair_kernel(
     KParams P, const S* __restrict__ Bin, S* __restrict__ Bout, const float* __restrict__ theta,
     const uint8_t* __restrict__ flags, double* __restrict__ obj) {
@@ -340,14 +341,26 @@ __global__ void __launch_bounds__(256) objective_kernel(KParams P, const S* __re
 // ---------------------------------------------------------------------------
 // adjoint step: lambda^n(x) from lambda^{n+1}(x + e_j) and f^n(x)
 // ---------------------------------------------------------------------------
-template <class L, int NS, bool MRT, class S, bool SRC = true>
+// One-shot design update fused into the adjoint step (Sec. 3.3, Eq.
+// gradient:update with the penalty of Eq. P): active when theta_out is set.
+// The node's gradient estimate g overwrites grad (instead of accumulating)
+// and, on design nodes, theta_out = clamp(theta + zeta (sign g - penalty
+// (1 - 2 theta)), 0, 1) in FP32.  Each thread reads and writes only its own
+// node's theta, after its last read of it.
+struct OneShot {
+  const uint8_t* design;
+  float* theta_out;
+  float zeta, penalty, sign;
+};
+
+template <class L, int NS, bool MRT, class S, int SRC = 2>
 __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __restrict__ lam_in,
                                              const S* __restrict__ Bn, float* __restrict__ lam_out,
                                              const float* __restrict__ theta,
                                              const uint8_t* __restrict__ flags,
                                              double* __restrict__ grad, float ws,
                                              const double* __restrict__ stat_n, int has_next,
-                                             long long idx) {
+                                             long long idx, const OneShot& os) {
   using Ops = NodeOps<L, NS, MRT>;
   using LS = typename Ops::LS;
   constexpr int Q = Ops::Q, QS = Ops::QS, NSA = Ops::NSA;
@@ -380,31 +393,42 @@ __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __re
     }
   };
   float lam[Q], lamg[NSA][QS], dth;
-  Ops::template reverse<decltype(load), SRC>(P, type, theta[idx], geo.y, d, g, load, ws, cbar, lam,
-                                             lamg, dth);
+  const float th = theta[idx];
+  Ops::template reverse<decltype(load), SRC>(P, type, th, geo.y, d, g, load, ws, cbar, lam, lamg,
+                                             dth);
 #pragma unroll
   for (int i = 0; i < Q; ++i) st(lam_out + (long long)i * P.N + idx, lam[i]);
 #pragma unroll
   for (int s = 0; s < NS; ++s)
 #pragma unroll
     for (int i = 0; i < QS; ++i) st(lam_out + (long long)(Q + s * QS + i) * P.N + idx, lamg[s][i]);
-  if (type == FLUID || type == INLET || type == OUTLET) grad[idx] += (double)dth;
+  const bool has_theta = type == FLUID || type == INLET || type == OUTLET;
+  if (os.theta_out != nullptr) {
+    const float gk = has_theta ? dth : 0.0f;
+    grad[idx] = (double)gk;
+    if (os.design[idx]) {
+      const float tn = th + os.zeta * (os.sign * gk - os.penalty * (1.0f - 2.0f * th));
+      os.theta_out[idx] = fminf(fmaxf(tn, 0.0f), 1.0f);
+    }
+  } else if (has_theta) {
+    grad[idx] += (double)dth;
+  }
 }
 
-// SRC: the step carries an objective source (ws != 0); most steps of a long
-// horizon with a short objective window do not, and the kernel without the
-// source terms holds fewer registers across the lambda gathers
-template <class L, int NS, bool MRT, class S, bool SRC>
-__global__ void __launch_bounds__(ALBM_ADJ_BLOCK, SRC ? ALBM_ADJOINT_MINB : ALBM_ADJOINT_MINB_NOSRC) adjoint_kernel(KParams P, const float* __restrict__ lam_in,
+// SRC: source form compiled in (obj_kind of ws != 0); most steps of a long
+// horizon with a short objective window carry none, and the kernels with
+// fewer source terms hold fewer registers across the lambda gathers
+template <class L, int NS, bool MRT, class S, int SRC>
+__global__ void __launch_bounds__(ALBM_ADJ_BLOCK, SRC == 2 ? ALBM_ADJOINT_MINB : ALBM_ADJOINT_MINB_NOSRC) adjoint_kernel(KParams P, const float* __restrict__ lam_in,
                                                       const S* __restrict__ Bn,
                                                       float* __restrict__ lam_out,
                                                       const float* __restrict__ theta,
                                                       const uint8_t* __restrict__ flags,
                                                       double* __restrict__ grad, float ws,
                                                       const double* __restrict__ stat_n,
-                                                      int has_next) {
+                                                      int has_next, OneShot os) {
   adjoint_body<L, NS, MRT, S, SRC>(P, lam_in, Bn, lam_out, theta, flags, grad, ws, stat_n, has_next,
-                                   (long long)blockIdx.x * blockDim.x + threadIdx.x);
+                                   (long long)blockIdx.x * blockDim.x + threadIdx.x, os);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,12 +477,19 @@ __global__ void __launch_bounds__(256, 4) primal_batch_kernel(const __grid_const
   const long long idx = (long long)block * blockDim.x + threadIdx.x;
   // the same specialisation as the single-instance launch of this step, so
   // that batched and lone results agree bit for bit
-  if (D.obj != nullptr)
-    primal_body<L, NS, MRT, S, true>(D.P, (const S*)D.Bin, (S*)D.Bout, D.theta, D.flags, D.obj, idx,
-                                     block);
-  else
-    primal_body<L, NS, MRT, S, false>(D.P, (const S*)D.Bin, (S*)D.Bout, D.theta, D.flags, D.obj,
-                                      idx, block);
+  switch (obj_kind(D.obj != nullptr, D.P.objective)) {
+    case 0:
+      primal_body<L, NS, MRT, S, 0>(D.P, (const S*)D.Bin, (S*)D.Bout, D.theta, D.flags, D.obj, idx,
+                                    block);
+      break;
+    case 1:
+      primal_body<L, NS, MRT, S, 1>(D.P, (const S*)D.Bin, (S*)D.Bout, D.theta, D.flags, D.obj, idx,
+                                    block);
+      break;
+    default:
+      primal_body<L, NS, MRT, S, 2>(D.P, (const S*)D.Bin, (S*)D.Bout, D.theta, D.flags, D.obj, idx,
+                                    block);
+  }
 }
 
 template <class L, int NS, bool MRT, class S>
@@ -466,12 +497,19 @@ __global__ void __launch_bounds__(256, 2) adjoint_batch_kernel(const __grid_cons
   const InstanceDesc& D = args.inst[batch_instance(args)];
   const long long block = (long long)blockIdx.x - D.block_begin;
   const long long idx = block * blockDim.x + threadIdx.x;
-  if (D.ws != 0.0f)
-    adjoint_body<L, NS, MRT, S, true>(D.P, D.lam_in, (const S*)D.Bin, D.lam_out, D.theta, D.flags,
-                                      D.grad, D.ws, D.stat_n, D.has_next, idx);
-  else
-    adjoint_body<L, NS, MRT, S, false>(D.P, D.lam_in, (const S*)D.Bin, D.lam_out, D.theta, D.flags,
-                                       D.grad, D.ws, D.stat_n, D.has_next, idx);
+  switch (obj_kind(D.ws != 0.0f, D.P.objective)) {
+    case 0:
+      adjoint_body<L, NS, MRT, S, 0>(D.P, D.lam_in, (const S*)D.Bin, D.lam_out, D.theta, D.flags,
+                                     D.grad, D.ws, D.stat_n, D.has_next, idx, OneShot{});
+      break;
+    case 1:
+      adjoint_body<L, NS, MRT, S, 1>(D.P, D.lam_in, (const S*)D.Bin, D.lam_out, D.theta, D.flags,
+                                     D.grad, D.ws, D.stat_n, D.has_next, idx, OneShot{});
+      break;
+    default:
+      adjoint_body<L, NS, MRT, S, 2>(D.P, D.lam_in, (const S*)D.Bin, D.lam_out, D.theta, D.flags,
+                                     D.grad, D.ws, D.stat_n, D.has_next, idx, OneShot{});
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -561,6 +599,7 @@ struct StepArgs {
   int post;
   unsigned long long* count;
   int* err;             // set by a staged kernel whose bounded wait expired
+  OneShot os;           // fused one-shot update of the adjoint step (theta_out null: off)
 };
 
 struct KernelSet {
@@ -607,15 +646,20 @@ struct Launch {
     if constexpr (sizeof(S) == 2) {
       if (paired(P)) {
         const unsigned nb = (unsigned)((P.N / 2 + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK);
-        auto k = a.obj != nullptr ? primal_pair_kernel<L, NS, MRT, S, true>
-                                  : primal_pair_kernel<L, NS, MRT, S, false>;
+        const int ok = obj_kind(a.obj != nullptr, P.objective);
+        auto k = ok == 0 ? primal_pair_kernel<L, NS, MRT, S, 0>
+                 : ok == 1 ? primal_pair_kernel<L, NS, MRT, S, 1>
+                           : primal_pair_kernel<L, NS, MRT, S, 2>;
         k<<<nb, ALBM_PRIMAL_BLOCK, 0, st>>>(P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags,
                                             a.obj);
         return cudaGetLastError();
       }
     }
     const unsigned nb = (unsigned)((P.N + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK);
-    auto k = a.obj != nullptr ? primal_kernel<L, NS, MRT, S, true> : primal_kernel<L, NS, MRT, S, false>;
+    const int ok = obj_kind(a.obj != nullptr, P.objective);
+    auto k = ok == 0 ? primal_kernel<L, NS, MRT, S, 0>
+             : ok == 1 ? primal_kernel<L, NS, MRT, S, 1>
+                       : primal_kernel<L, NS, MRT, S, 2>;
     k<<<nb, ALBM_PRIMAL_BLOCK, 0, st>>>(P, (const S*)a.Bin, (S*)a.Bout, a.theta, a.flags, a.obj);
     return cudaGetLastError();
   }
@@ -626,9 +670,12 @@ struct Launch {
   }
   static cudaError_t adjoint(const KParams& P, const StepArgs& a, cudaStream_t st) {
     const unsigned nb = (unsigned)((P.N + ALBM_ADJ_BLOCK - 1) / ALBM_ADJ_BLOCK);
-    auto k = a.ws != 0.0f ? adjoint_kernel<L, NS, MRT, S, true> : adjoint_kernel<L, NS, MRT, S, false>;
+    const int sk = obj_kind(a.ws != 0.0f, P.objective);
+    auto k = sk == 0 ? adjoint_kernel<L, NS, MRT, S, 0>
+             : sk == 1 ? adjoint_kernel<L, NS, MRT, S, 1>
+                       : adjoint_kernel<L, NS, MRT, S, 2>;
     k<<<nb, ALBM_ADJ_BLOCK, 0, st>>>(P, a.lam_in, (const S*)a.Bin, a.lam_out, a.theta, a.flags,
-                                     a.grad, a.ws, a.stat_n, a.has_next);
+                                     a.grad, a.ws, a.stat_n, a.has_next, a.os);
     return cudaGetLastError();
   }
   static cudaError_t exportf(const KParams& P, const StepArgs& a, cudaStream_t st) {

@@ -33,6 +33,15 @@ enum : uint8_t { FLUID = 0, WALL = 1, INLET = 2, OUTLET = 3, HOT = 4 };
 enum { OBJ_NONE = 0, OBJ_DISSIPATION = 1, OBJ_VARIANCE = 2, OBJ_HEATFLUX_DP = 3, OBJ_MIXFLUX = 4 };
 enum { POR_LINEAR = 0, POR_POWER = 1, POR_RAMP = 2 };
 
+// Objective form a launch compiles in: 0 when the step records or sources no
+// objective, 2 for the dissipation (a term at every fluid node), 1 for the
+// outlet/inlet objectives (terms at boundary nodes only, so the kernel keeps
+// no per-population source in registers).  Host and batched launches use
+// the same rule, so a node gets the same code alone or batched.
+__host__ __device__ inline int obj_kind(bool active, int objective) {
+  return !active ? 0 : (objective == OBJ_DISSIPATION ? 2 : 1);
+}
+
 #ifndef ALBM_ADJ_TWO_PHASE
 #define ALBM_ADJ_TWO_PHASE 1
 #endif
@@ -269,8 +278,11 @@ struct NodeOps {
 
   // -------------------------------------------------------------------------
   // Forward: W^x applied to d (fluid deviations) and g (scalars) in place.
-  // obj1/obj2 receive this node's objective terms F^x(f^n(x)).
+  // obj1/obj2 receive this node's objective terms F^x(f^n(x)).  OBJ is the
+  // objective form compiled in (see obj_kind): 0 none, 1 outlet/inlet
+  // objectives only, 2 all (with the dissipation of every fluid node).
   // -------------------------------------------------------------------------
+  template <int OBJ = 2>
   __device__ static __forceinline__ void forward(const KParams& P, uint8_t type, float th, int y,
                                                  float* d, float (*g)[QS], bool want_obj,
                                                  double& obj1, double& obj2) {
@@ -303,7 +315,7 @@ struct NodeOps {
     } else {
       moments(d, rho, drho, u);
     }
-    if (want_obj && P.objective == OBJ_DISSIPATION && type == FLUID) {
+    if (OBJ == 2 && want_obj && P.objective == OBJ_DISSIPATION && type == FLUID) {
       obj1 += (double)dissipation(P, d, rho, drho, u);
     }
     float G, dG;
@@ -340,7 +352,7 @@ struct NodeOps {
       float T, den;
       if (type == OUTLET) {
         scalar_outlet(g[s], v, T, den);
-        if (want_obj && s == 0) {
+        if (OBJ != 0 && want_obj && s == 0) {
           if (P.objective == OBJ_VARIANCE) {
             obj1 += (double)T;
             obj2 += (double)T * (double)T;
@@ -420,10 +432,11 @@ struct NodeOps {
   // -------------------------------------------------------------------------
   // The adjoint weights are fetched by load(a, b) only after the forward
   // quantities are recomputed (two phases: f^n first, lambda^{n+1} second),
-  // which bounds the number of values live in registers at once.  SRC =
-  // false compiles the objective source terms out, for steps whose weight ws
-  // is zero (same values: the sources only add exact zeros then).
-  template <class Loader, bool SRC = true>
+  // which bounds the number of values live in registers at once.  SRC is
+  // the source form compiled in (see obj_kind): 0 none, for steps whose
+  // weight ws is zero (the sources would add exact zeros), 1 outlet/inlet
+  // objectives only, 2 all (the dissipation source of every fluid node).
+  template <class Loader, int SRC = 2>
   __device__ static __forceinline__ void reverse(const KParams& P, uint8_t type, float th, int y,
                                                  const float* d_in, float (*g)[QS],
                                                  const Loader& load, float ws, float cbar,
@@ -479,8 +492,8 @@ struct NodeOps {
       }
     }
     // ---- objective sources ws * dF^x ----
-    if (SRC && ws != 0.0f) {
-      if (P.objective == OBJ_DISSIPATION && type == FLUID) {
+    if (SRC != 0 && ws != 0.0f) {
+      if (SRC == 2 && P.objective == OBJ_DISSIPATION && type == FLUID) {
         float Pi[3][3];
         pi_neq(d, rho, drho, u, Pi);
         float s2 = 0.0f, tr = 0.0f;
