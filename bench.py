@@ -20,8 +20,9 @@ aggregate.
 Other workloads (--workload): exchanger3d (512x256x256 BGK + D3Q7, heat
 flux), batch64 (64 instances through the batched autograd Function), serve
 (continuous batching of Poisson-arriving requests), oneshot (the one-shot
-optimisation of Sec. 3.3 on the exchanger) and meshes (primal and adjoint
-kernel rates on the paper's 400K / 3M / 12M scaling meshes).
+optimisation of Sec. 3.3 on the exchanger), meshes (primal and adjoint
+kernel rates on the paper's 400K / 3M / 12M scaling meshes) and paper (the
+paper's empty mixer and exchanger channels against its printed values).
 """
 from __future__ import annotations
 
@@ -551,6 +552,36 @@ def run_meshes(args):
     return 0
 
 
+def run_paper(args):
+    """The paper's empty mixer and exchanger channels (Tab. tab:cases) for the
+    iterations Tab. tab:results lists: J and outlet statistics against the
+    printed Empty rows, and the primal MLUPS of the run."""
+    import torch
+    from paper_1501_04741_gb300.albm import Solver
+    from tests.test_gpu_paper_tables import _golden, outlet_stats
+    rows = []
+    gold = _golden()
+    for case, P in (("mixer", inputs.paper_mixer_empty()), ("exchanger", inputs.paper_exchanger_empty())):
+        th = torch.zeros(P.n_nodes, dtype=torch.float32, device="cuda")
+        with Solver(P, th) as s:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.primal_step(P.nsteps)
+            J = s.objective()
+            dt = time.perf_counter() - t0
+            um, us, Tm, Ts = outlet_stats(s, P)
+        ref = gold[case]
+        rows.append({"case": case, "dims": list(P.dims), "steps": P.nsteps, "objective": P.objective,
+                     "J": J, "J_paper": ref["J"], "u_mean": um, "u_sd": us, "u_paper": ref["u"],
+                     "T_mean": Tm, "T_sd": Ts, "T_paper": ref["T"],
+                     "primal_MLUPS": P.n_nodes * P.nsteps / dt / 1e6})
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"metric": "paper empty channels vs Tab. tab:results", "workload": "paper",
+                      "unit": UNIT, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """A few launches of each kernel on a lattice that still exceeds L2."""
     import torch
@@ -584,7 +615,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="mixer3d",
-                    choices=["mixer3d", "exchanger3d", "batch64", "serve", "oneshot", "meshes"])
+                    choices=["mixer3d", "exchanger3d", "batch64", "serve", "oneshot", "meshes",
+                             "paper"])
     ap.add_argument("--count", type=int, default=0, help="instances (batch64) or requests (serve)")
     ap.add_argument("--size-scale", type=float, default=1.0, help="batch64: linear size factor")
     ap.add_argument("--rates", default="2,20,200", help="serve: arrival rates per second")
@@ -607,6 +639,8 @@ def main(argv=None):
         return run_oneshot(args)
     if args.workload == "meshes":
         return run_meshes(args)
+    if args.workload == "paper":
+        return run_paper(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

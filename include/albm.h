@@ -65,7 +65,8 @@ typedef enum {
   LBM_OBJ_DISSIPATION = 1, /* sum over FLUID nodes of 2 rho nu S:S            */
   LBM_OBJ_VARIANCE = 2,    /* outlet variance of scalar 0                     */
   LBM_OBJ_HEATFLUX_DP = 3, /* outlet sum u_x T (Eq. exchanger:obj) - 0.1 dp   */
-  LBM_OBJ_MIXFLUX = 4      /* outlet sum u_x (1 - T^2) (Eq. mixing:obj)        */
+  LBM_OBJ_MIXFLUX = 4,     /* outlet sum u_x (1 - T^2) (Eq. mixing:obj)        */
+  LBM_OBJ_HEATFLUX = 5     /* outlet sum u_x T alone (Eq. exchanger:obj)       */
 } lbm_objective_kind;
 
 /* Node types of the uint8 flag array (Sec. 3: interior, inlet/outlet, wall). */
@@ -93,7 +94,9 @@ typedef struct {
   double alpha_fluid;   /* scalar diffusivity at theta = 0                    */
   double alpha_solid;   /* scalar diffusivity at theta = 1 (Sec. 3.2 interp.) */
   int scalar_inlet;     /* 0: zero; 1: halves (0 for y < Ly/2, else 1; odd
-                           scalars carry the complement)                     */
+                           scalars carry the complement 1 - c); 2: signed
+                           (-1 for y < Ly/2, else +1, the paper's mixer
+                           inlet, Sec. 4.1; odd scalars carry -c)            */
   int hot[4];           /* x0, x1, z0, z1 of the T_hot patch on y = 0; x1<=x0
                            means none                                        */
   double T_hot;

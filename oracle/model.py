@@ -176,14 +176,17 @@ class Model:
         return torch.stack(rows), T
 
     def inlet_scalar(self, s: int, y):
-        """Inlet value of scalar s at row y ("halves": 0 below Ly/2, 1 above;
-        odd scalars carry the complement)."""
+        """Inlet value of scalar s at row y ("halves": 0 below Ly/2, 1 above,
+        odd scalars carry the complement 1 - c; "signed": -1 below Ly/2, +1
+        above as in the paper's mixer (Sec. 4.1), odd scalars carry -c)."""
         P = self.P
+        upper = (y >= P.dims[1] // 2).to(DT)
         if P.scalar_inlet == "halves":
-            c = (y >= P.dims[1] // 2).to(DT)
-        else:
-            c = torch.zeros(y.shape, dtype=DT)
-        return 1 - c if (s % 2 == 1 and P.scalar_inlet == "halves") else c
+            return 1 - upper if s % 2 == 1 else upper
+        if P.scalar_inlet == "signed":
+            c = 2 * upper - 1
+            return -c if s % 2 == 1 else c
+        return torch.zeros(y.shape, dtype=DT)
 
     # --- the node operator --------------------------------------------------
     def macroscopic(self, F, theta, flags):
@@ -262,6 +265,7 @@ class Model:
           c the outlet value T*.
         * heatflux_dp: sum over OUTLET nodes of v_x T* (Eq. exchanger:obj)
           minus 0.1 (mean inlet rho - rho_out)/3.
+        * heatflux: sum over OUTLET nodes of v_x T* alone (Eq. exchanger:obj).
         * mixflux: sum over OUTLET nodes of v_x (1 - T*^2) (Eq. mixing:obj).
         """
         P = self.P
@@ -286,6 +290,8 @@ class Model:
             inl = (flags == INLET).to(DT)
             rho_in_mean = (m["rho"] * inl).sum() / n_inlet
             return (vx * c * out).sum() - 0.1 * (rho_in_mean - P.rho_out) / 3.0
+        if kind == "heatflux":
+            return (vx * c * out).sum()
         if kind == "mixflux":
             return (vx * (1 - c * c) * out).sum()
         raise ValueError(kind)

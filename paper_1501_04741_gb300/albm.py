@@ -23,7 +23,9 @@ LATTICE = {"D2Q9": 0, "D3Q19": 1}
 COLLISION = {"BGK": 0, "MRT": 1}
 PRECISION = {"fp32": 0, "bf16": 1, "fp16": 2}
 POROSITY = {"linear": 0, "power": 1, "ramp": 2}
-OBJECTIVE = {"none": 0, "dissipation": 1, "variance": 2, "heatflux_dp": 3, "mixflux": 4}
+OBJECTIVE = {"none": 0, "dissipation": 1, "variance": 2, "heatflux_dp": 3, "mixflux": 4,
+             "heatflux": 5}
+SCALAR_INLET = {"zero": 0, "halves": 1, "signed": 2}
 KERNEL = {"auto": 0, "plain": 1, "tiles": 2, "async": 3}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
           4: "LBM_ERR_NONFINITE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
@@ -131,7 +133,7 @@ def make_params(P: Problem, mem_budget: float = 0.0) -> LbmParams:
     p.nscalars = int(P.nscalars)
     p.alpha_fluid = float(P.alpha_fluid)
     p.alpha_solid = float(P.alpha_solid)
-    p.scalar_inlet = 1 if P.scalar_inlet == "halves" else 0
+    p.scalar_inlet = SCALAR_INLET[P.scalar_inlet]
     hot = tuple(P.hot) if P.hot else (0, 0, 0, 0)
     for a in range(4):
         p.hot[a] = int(hot[a])

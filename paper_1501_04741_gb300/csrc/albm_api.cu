@@ -473,10 +473,11 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   else if (p.precision < 0 || p.precision > 2) st = bad("precision must be FP32, BF16 or FP16");
   else if (p.nsteps < 0) st = bad("nsteps must be >= 0");
   else if (p.obj_window < 0 || p.obj_window > p.nsteps + 1) st = bad("obj_window out of range");
-  else if (p.objective < 0 || p.objective > 4) st = bad("unknown objective");
+  else if (p.objective < 0 || p.objective > 5) st = bad("unknown objective");
   else if (p.objective >= LBM_OBJ_VARIANCE && (p.nscalars < 1 || !p.inlet_outlet))
     st = bad("outlet objectives need a scalar lattice and inlet_outlet");
   else if (p.porosity < 0 || p.porosity > 2) st = bad("unknown porosity law");
+  else if (p.scalar_inlet < 0 || p.scalar_inlet > 2) st = bad("unknown scalar inlet profile");
   else if (p.porosity == LBM_POR_POWER && p.porosity_q < 1.0) st = bad("power porosity needs q >= 1");
   else if (p.inlet_outlet && (p.nx < 3 || !(p.u_in < 1.0) || !(p.rho_out > 0.0)))
     st = bad("inlet_outlet needs nx >= 3, u_in < 1 and rho_out > 0");

@@ -170,7 +170,7 @@ extern "C" lbm_status lbm_state_objective_noalloc(const lbm_params* pp, const fl
     return fail(LBM_ERR_ARG, "bad lattice sizes");
   if (p.nscalars < 0 || p.nscalars > (p.lattice == LBM_D3Q19 ? 2 : 1))
     return fail(LBM_ERR_ARG, "nscalars out of range");
-  if (!(p.tau > 0.5) || p.objective < LBM_OBJ_DISSIPATION || p.objective > LBM_OBJ_MIXFLUX)
+  if (!(p.tau > 0.5) || p.objective < LBM_OBJ_DISSIPATION || p.objective > LBM_OBJ_HEATFLUX)
     return fail(LBM_ERR_ARG, "tau must exceed 1/2 and an objective must be set");
   if (p.objective >= LBM_OBJ_VARIANCE && p.nscalars < 1)
     return fail(LBM_ERR_ARG, "outlet objectives need a scalar lattice");

@@ -30,7 +30,14 @@
 namespace albm {
 
 enum : uint8_t { FLUID = 0, WALL = 1, INLET = 2, OUTLET = 3, HOT = 4 };
-enum { OBJ_NONE = 0, OBJ_DISSIPATION = 1, OBJ_VARIANCE = 2, OBJ_HEATFLUX_DP = 3, OBJ_MIXFLUX = 4 };
+enum {
+  OBJ_NONE = 0,
+  OBJ_DISSIPATION = 1,
+  OBJ_VARIANCE = 2,
+  OBJ_HEATFLUX_DP = 3,
+  OBJ_MIXFLUX = 4,
+  OBJ_HEATFLUX = 5
+};
 enum { POR_LINEAR = 0, POR_POWER = 1, POR_RAMP = 2 };
 
 // Objective form a launch compiles in: 0 when the step records or sources no
@@ -268,10 +275,17 @@ struct NodeOps {
     }
   }
 
+  // prescribed inlet value of scalar s on row y: 1 halves (0 below ny/2, 1
+  // above, odd scalars 1 - c), 2 signed (-1 below, +1 above, odd scalars -c)
   __device__ static __forceinline__ float inlet_value(const KParams& P, int s, int y) {
+    const bool upper = y >= P.ny / 2;
     if (P.scalar_inlet == 1) {
-      const float c = (y >= P.ny / 2) ? 1.0f : 0.0f;
+      const float c = upper ? 1.0f : 0.0f;
       return (s & 1) ? 1.0f - c : c;
+    }
+    if (P.scalar_inlet == 2) {
+      const float c = upper ? 1.0f : -1.0f;
+      return (s & 1) ? -c : c;
     }
     return 0.0f;
   }
@@ -356,7 +370,7 @@ struct NodeOps {
           if (P.objective == OBJ_VARIANCE) {
             obj1 += (double)T;
             obj2 += (double)T * (double)T;
-          } else if (P.objective == OBJ_HEATFLUX_DP) {
+          } else if (P.objective == OBJ_HEATFLUX_DP || P.objective == OBJ_HEATFLUX) {
             obj1 += (double)v[0] * (double)T;
           } else if (P.objective == OBJ_MIXFLUX) {
             obj1 += (double)v[0] * (1.0 - (double)T * (double)T);
@@ -520,7 +534,7 @@ struct NodeOps {
         const float T0 = T[0];
         if (P.objective == OBJ_VARIANCE) {
           dT0 = ws * 2.0f * (T0 - cbar) * P.inv_A_out;
-        } else if (P.objective == OBJ_HEATFLUX_DP) {
+        } else if (P.objective == OBJ_HEATFLUX_DP || P.objective == OBJ_HEATFLUX) {
           dv[0] += ws * T0;
           dT0 = ws * v[0];
         } else if (P.objective == OBJ_MIXFLUX) {

@@ -40,6 +40,12 @@ def _cases():
         "d3q19_bgk_exchanger": exch,
         "d3q19_mrt_exchanger_power": exch.replace(collision="MRT", porosity="power",
                                                   porosity_q=3.0),
+        # the paper's own channels (Tab. tab:cases): signed inlet + mixing
+        # flux, and the heat flux without the pressure term
+        "d3q19_mrt_paper_mixer": inputs.scaled(inputs.paper_mixer_empty(), (23, 10, 10),
+                                               nsteps=40),
+        "d3q19_mrt_paper_exchanger": inputs.scaled(inputs.paper_exchanger_empty(), (14, 10, 9),
+                                                   nsteps=120),
     }
 
 

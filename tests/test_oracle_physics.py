@@ -304,6 +304,42 @@ def test_heat_flux_pressure_drop_term():
     Tstar = T * float((m.sl.w * phiU)[known].sum()) / (1 - float((m.sl.w * phi_out)[~known].sum()))
     expect = A * ux_out * Tstar - 0.1 * (rho0 - 1.0) / 3.0
     assert abs(float(o.F_obj(F)) - expect) < 1e-13
+    # the heat flux alone (Eq. exchanger:obj) has no pressure term
+    oh = Oracle(P.replace(objective="heatflux"), np.zeros(P.dims[::-1], np.float32))
+    assert abs(float(oh.F_obj(F)) - A * ux_out * Tstar) < 1e-13
+
+
+def test_signed_inlet_values_after_collision():
+    # the paper's mixer inlet (Sec. 4.1): T = -1 for y < Ly/2 and +1 above;
+    # the second scalar carries -T
+    P = _mixer_small(collision="BGK", scalar_inlet="signed")
+    o = Oracle(P, np.zeros(P.dims[::-1], np.float32))
+    F = _rand_state(o, 6, scale=0.01)
+    post = o.collide(F).reshape(o.model.M, -1)
+    m = o.model
+    inl = o.flags == INLET
+    T0 = post[m.Q:m.Q + m.Qs].sum(0)
+    T1 = post[m.Q + m.Qs:].sum(0)
+    c = torch.where(o.y >= P.dims[1] // 2, 1.0, -1.0).double()
+    assert (T0[inl] - c[inl]).abs().max() < 1e-14
+    assert (T1[inl] + c[inl]).abs().max() < 1e-14
+
+
+@pytest.mark.parametrize("coll", ["BGK", "MRT"])
+def test_signed_inlet_field_is_antisymmetric(coll):
+    # The channel, its walls and its inflow are symmetric under y -> Ly-1-y
+    # (Ly even) and the signed inlet changes sign under it, so the scalar
+    # field (a linear response to the inlet, starting from 0) is odd in y at
+    # every step, and its outlet mean vanishes.
+    P = inputs.scaled(inputs.mixer3d(), (12, 8, 6), nsteps=30, obj_window=0,
+                      collision=coll, scalar_inlet="signed", nscalars=1)
+    o = Oracle(P, np.zeros(P.dims[::-1], np.float32))
+    _, traj = o.primal(keep=False)
+    F = traj[-1]
+    m = o.model
+    T = F[m.Q:m.Q + m.Qs].sum(0)                       # (Lz, Ly, Lx)
+    assert float(T.abs().max()) > 1e-3
+    assert float((T + T.flip(1)).abs().max()) < 1e-13
 
 
 def test_outlet_variance_of_a_two_level_profile():
