@@ -4,9 +4,10 @@ Test infrastructure only (see ``oracle/__init__``).
 
 * D3Q19 is the list e1..e19 of Sec. 3 in the paper's order (index 0 = e1 =
   rest vector).
-* D3Q7 is e1..e7 ("for the heat transfer equation we use the first 7").
+* D3Q7 is e1..e7, the first seven vectors of that list (Sec. 3).
 * D2Q9 is the set of z = 0 members of the D3Q19 list in paper order,
-  {e1, e2, e3, e4, e5, e8, e9, e10, e11} ("reduced to 9" in 2D, Sec. 3).
+  {e1, e2, e3, e4, e5, e8, e9, e10, e11} (Sec. 3 reduces the set to nine
+  vectors in 2D).
 * Weights are the standard ones of each set (the paper does not print them):
   D2Q9 4/9, 1/9, 1/36; D3Q19 1/3, 1/18, 1/36 (c_s^2 = 1/3); D3Q7 1/4, 1/8
   (c_s^2 = 1/4).  Tests pin them by the isotropy conditions.
