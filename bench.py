@@ -59,9 +59,9 @@ def bytes_per_node(M: int, storage: int, kind: str) -> int:
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # the ncu capture of the 256x128x64 profile case, scaled by the node count to
 # the 256x128x128 lattice (traffic grows with the nodes); valid for the FP32
-# mixer kernels as captured: the specialisations without objective terms
-# (primal OBJ = false, adjoint SRC = false), which run 95 % of the steps.
-TRAFFIC_MIXER_FP32 = {"primal": 1.0314e9, "adjoint": 1.6750e9}
+# mixer kernels as captured: the forms without objective terms (primal
+# OBJ = 0, adjoint SRC = 0), which run 95 % of the steps.
+TRAFFIC_MIXER_FP32 = {"primal": 1.0311e9, "adjoint": 1.6752e9}
 
 
 def workload(args) -> inputs.Problem:
