@@ -18,8 +18,10 @@ The oracle is plain PyTorch CPU code in float64:
   form of Eqs. "adjoint:iteration"/"adjoint:operator" with the gradient of
   Eq. "adjoint:derivative" accumulated over the steps), the frozen-state
   ALBS mode, the one-shot optimisation of Sec. 3.3 with the penalty of
-  Eq. P and the threshold scan of Sec. 3.2, and a central
-  finite-difference driver.
+  Eq. P and the threshold scan of Sec. 3.2, the MMA design loop of
+  Sec. 3.3, and a central finite-difference driver.
+* ``mma``      - the Method of Moving Asymptotes (Svanberg's method, which
+  Sec. 3.3 cites without formulas) for box-bounded design variables.
 
 The adjoint collision is the vector-Jacobian product of W^x, taken by
 PyTorch's reverse-mode autodiff (a library primitive, in the role TAPENADE

@@ -276,6 +276,31 @@ class Oracle:
         """F(f^N) of the thresholded design for every level eta."""
         return [self.steady_objective(nsteps, self.threshold(theta, e, design)) for e in etas]
 
+    # --- MMA design iterations (Sec. 3.3, oracle.mma) ------------------------
+    def mma(self, iters, maximize=True, design=None, prm=None):
+        """MMA as Sec. 3.3 runs it: per design iteration a full solve (here
+        the N-step primal and the unsteady adjoint, exact dJ/dtheta), then one
+        MMA update of theta on the design nodes (``oracle.mma.update``; a
+        maximised J is minimised as -J).  Returns (theta, [J per iteration],
+        MMA state)."""
+        from . import mma as M
+        prm = prm or M.MMAParams()
+        th = self.theta.numpy().astype(np.float64).copy()
+        state = M.start(th)
+        mask = None if design is None else np.asarray(design).reshape(-1).astype(bool)
+        hist = []
+        saved = self.theta
+        try:
+            for _ in range(int(iters)):
+                self.theta = torch.as_tensor(th)
+                J, g, _ = self.gradient()
+                hist.append(J)
+                g = g.reshape(-1).numpy()
+                th = M.update(state, th, -g if maximize else g, mask, prm)
+        finally:
+            self.theta = saved
+        return th.reshape(self.shape), hist, state
+
     # --- finite differences -------------------------------------------------
     def fd(self, index, h=1e-6, nsteps=None):
         """Central difference of J w.r.t. theta at one flat node index."""

@@ -609,7 +609,7 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   if (budget <= 0) {
     size_t fr = 0, tot = 0;
     CKC(cudaMemGetInfo(&fr, &tot));
-    budget = 0.85 * (double)fr;
+    budget = 0.90 * (double)fr;
   }
   h->max_bufs = (int)std::max(3.0, std::floor(budget / (double)h->state_bytes));
   // level-1 checkpoint stride: given, or every state if all fit, else

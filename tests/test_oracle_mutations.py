@@ -178,3 +178,44 @@ def test_threshold_tie_to_solid_is_caught(monkeypatch):
     monkeypatch.setattr(Oracle, "threshold", staticmethod(bad))
     with pytest.raises(AssertionError):
         TO.test_threshold_rule()
+
+
+# ---- MMA (Sec. 3.3, oracle.mma) --------------------------------------------
+def test_mma_swapped_approximation_terms_are_caught(monkeypatch):
+    from oracle import mma as M
+    from tests import test_oracle_mma as TM
+    orig = M.subproblem
+
+    def bad(x, g, L, U, prm=M.MMAParams()):
+        return orig(x, -np.asarray(g), L, U, prm)       # p and q exchanged
+    monkeypatch.setattr(M, "subproblem", bad)
+    with pytest.raises(AssertionError):
+        TM.test_approximation_is_first_order_exact_and_convex()
+
+
+def test_mma_inverted_oscillation_rule_is_caught(monkeypatch):
+    import dataclasses
+
+    from oracle import mma as M
+    from tests import test_oracle_mma as TM
+    orig = M.MMAParams
+    # asymptotes farther when a variable oscillates, closer when it does not
+    monkeypatch.setattr(M, "MMAParams", lambda: dataclasses.replace(orig(), s_dec=1.2, s_inc=0.7))
+    with pytest.raises(AssertionError):
+        TM.test_converges_on_a_separable_quadratic()
+
+
+def test_mma_closed_form_with_swapped_asymptotes_is_caught(monkeypatch):
+    from oracle import mma as M
+    from tests import test_oracle_mma as TM
+    orig = M.subproblem
+
+    def bad(x, g, L, U, prm=M.MMAParams()):
+        y, aux = orig(x, g, L, U, prm)
+        alpha, beta, p, q = aux
+        sp, sq = np.sqrt(p), np.sqrt(q)
+        y = np.clip((sp * U + sq * L) / (sp + sq), alpha, beta)
+        return y, aux
+    monkeypatch.setattr(M, "subproblem", bad)
+    with pytest.raises(AssertionError):
+        TM.test_subproblem_minimiser_matches_grid_search()
