@@ -21,8 +21,9 @@ Other workloads (--workload): exchanger3d (512x256x256 BGK + D3Q7, heat
 flux), batch64 (64 instances through the batched autograd Function), serve
 (continuous batching of Poisson-arriving requests), oneshot (the one-shot
 optimisation of Sec. 3.3 on the exchanger), meshes (primal and adjoint
-kernel rates on the paper's 400K / 3M / 12M scaling meshes) and paper (the
-paper's empty mixer and exchanger channels against its printed values).
+kernel rates on the paper's 400K / 3M / 12M scaling meshes), paper (the
+paper's empty mixer and exchanger channels against its printed values) and
+mma (MMA design iterations of Sec. 3.3 on the exchanger).
 """
 from __future__ import annotations
 
@@ -582,6 +583,50 @@ def run_paper(args):
     return 0
 
 
+def run_mma(args):
+    """MMA design iterations (Sec. 3.3) on the full exchanger: per iteration
+    the 1000 + 1000-step unsteady solve and one MMA update of theta."""
+    import torch
+    from paper_1501_04741_gb300.albm import Solver
+    P = inputs.exchanger3d()
+    theta = inputs.theta_grf(P, 0)
+    mask = inputs.design_mask(P).reshape(-1).astype(np.uint8)
+    iters = max(1, args.steps)
+    s = Solver(P, torch.from_numpy(theta.reshape(-1)).cuda(), stream=torch.cuda.Stream())
+    N = s.N
+    s.set_design(mask)
+    s.mma_reset()
+    for _ in range(args.warmup):
+        s.run()
+        s.mma_update(True, 0.2)
+    torch.cuda.synchronize()
+    hist = []
+    t0 = time.perf_counter()
+    t_upd = 0.0
+    for _ in range(iters):
+        s.run()
+        hist.append(s.objective())            # synchronises
+        t1 = time.perf_counter()
+        s.mma_update(True, 0.2)
+        torch.cuda.synchronize()
+        t_upd += time.perf_counter() - t1
+    wall = time.perf_counter() - t0
+    s.close()
+    upd_bytes = int(mask.sum()) * (4 * 2 + 4 * 8 + 8 + 1)
+    print(json.dumps({
+        "metric": "MMA design iterations, primal+adjoint MLUPS", "workload": "mma",
+        "value": 2.0 * N * P.nsteps * iters / wall / 1e6, "unit": UNIT, "n_gpus": 1,
+        "steps": iters, "warmup": args.warmup, "ms_per_step": 1e3 * wall / iters,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "mma", "lattice": P.lattice, "collision": P.collision,
+                   "dims": list(P.dims), "objective": P.objective, "steps_per_solve": P.nsteps,
+                   "move": 0.2, "design_nodes": int(mask.sum())},
+        "J_per_iteration": hist,
+        "update_ms": 1e3 * t_upd / iters,
+        "update_GB_s": upd_bytes / (t_upd / iters) / 1e9}), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """A few launches of each kernel on a lattice that still exceeds L2."""
     import torch
@@ -616,7 +661,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="mixer3d",
                     choices=["mixer3d", "exchanger3d", "batch64", "serve", "oneshot", "meshes",
-                             "paper"])
+                             "paper", "mma"])
     ap.add_argument("--count", type=int, default=0, help="instances (batch64) or requests (serve)")
     ap.add_argument("--size-scale", type=float, default=1.0, help="batch64: linear size factor")
     ap.add_argument("--rates", default="2,20,200", help="serve: arrival rates per second")
@@ -641,6 +686,8 @@ def main(argv=None):
         return run_meshes(args)
     if args.workload == "paper":
         return run_paper(args)
+    if args.workload == "mma":
+        return run_mma(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

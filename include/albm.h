@@ -296,6 +296,42 @@ lbm_status lbm_oneshot_eval(lbm_handle h, double* J, double* P);
  * Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
 lbm_status lbm_threshold_scan(lbm_handle h, const double* eta, int n, int nsteps, double* J_out);
 
+/* ---- MMA design iterations (Sec. 3.3) -------------------------------------
+ * The paper's second optimiser, Svanberg's Method of Moving Asymptotes,
+ * for 0 <= theta <= 1 without further constraints.  A design iteration is a
+ * full solve (lbm_run: primal, unsteady adjoint, dJ/dtheta) followed by
+ * lbm_mma_update, which changes theta on the design nodes (lbm_set_design):
+ *   asymptotes L < theta < U: iterations 0 and 1: theta -/+ 0.5; later the
+ *     previous distances scaled by 0.7 where theta oscillated (its last two
+ *     changes of opposite sign), by 1.2 where it moved monotonically, by 1
+ *     otherwise, and held within [0.01, 10];
+ *   move limits alpha = max(0, L + 0.1 (theta - L), theta - move),
+ *               beta  = min(1, U - 0.1 (U - theta), theta + move);
+ *   with g the gradient of f = -J when maximising, f = J otherwise,
+ *     p = (U - theta)^2 (1.001 g+ + 0.001 g- + 1e-5),
+ *     q = (theta - L)^2 (0.001 g+ + 1.001 g- + 1e-5),
+ *     theta <- min(max((sqrt p L + sqrt q U) / (sqrt p + sqrt q), alpha), beta),
+ *   the minimiser of the convex separable approximation
+ *   sum p / (U - theta) + q / (theta - L) on [alpha, beta].
+ * FP32 arithmetic; the history (two previous designs, last asymptotes:
+ * 4 N floats) is owned by the handle. */
+
+/* Start MMA at iteration 0 (allocates the history on first use). */
+lbm_status lbm_mma_reset(lbm_handle h);
+
+/* One MMA update with the handle's dJ/dtheta, after the adjoint has reached
+ * time 0 (lbm_run); then lbm_reset, so that the next solve starts from rest
+ * with the new theta.  maximize: nonzero maximises J.  move in (0, 1].
+ * Errors: LBM_ERR_STATE (no completed adjoint, no lbm_mma_reset, or a
+ * one-shot run active), LBM_ERR_ARG. */
+lbm_status lbm_mma_update(lbm_handle h, int maximize, double move);
+
+/* The same update with a caller's gradient dF/dtheta instead (N doubles,
+ * host or device; F is maximised when maximize is nonzero), e.g. of an
+ * objective composed outside the library; no completed adjoint is needed
+ * and the handle is not reset. */
+lbm_status lbm_mma_update_with(lbm_handle h, const double* grad, int maximize, double move);
+
 /* Binarise the handle's theta in place with one level eta (the rule of
  * lbm_threshold_scan) and reset the handle.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
 lbm_status lbm_threshold_apply(lbm_handle h, double eta);

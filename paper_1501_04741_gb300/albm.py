@@ -39,7 +39,8 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_theta", "lbm_
            "lbm_profile_read", "lbm_recompute_steps", "lbm_batch_primal_step",
            "lbm_batch_adjoint_step", "lbm_set_design", "lbm_oneshot_reset",
            "lbm_oneshot_step", "lbm_oneshot_eval", "lbm_threshold_scan",
-           "lbm_threshold_apply", "lbm_get_theta", "lbm_state_objective_noalloc",
+           "lbm_threshold_apply", "lbm_get_theta", "lbm_mma_reset", "lbm_mma_update",
+           "lbm_mma_update_with", "lbm_state_objective_noalloc",
            "lbm_noalloc_last_error"]
 
 
@@ -109,6 +110,9 @@ def lib():
         L.lbm_threshold_scan.argtypes = [vp, C.POINTER(d), i, i, C.POINTER(d)]
         L.lbm_threshold_apply.argtypes = [vp, d]
         L.lbm_get_theta.argtypes = [vp, vp]
+        L.lbm_mma_reset.argtypes = [vp]
+        L.lbm_mma_update.argtypes = [vp, i, d]
+        L.lbm_mma_update_with.argtypes = [vp, vp, i, d]
         L.lbm_state_objective_noalloc.argtypes = [C.POINTER(LbmParams), vp, vp, vp, vp,
                                                   C.POINTER(d)]
         L.lbm_noalloc_last_error.argtypes = []
@@ -387,6 +391,26 @@ class Solver:
 
     def threshold_apply(self, eta: float):
         self._check(self._L.lbm_threshold_apply(self._h, float(eta)))
+
+    # ---- MMA design iterations (Sec. 3.3) --------------------------------------
+    def mma_reset(self):
+        self._check(self._L.lbm_mma_reset(self._h))
+
+    def mma_update(self, maximize: bool = True, move: float = 0.5):
+        """One MMA update of theta with dJ/dtheta of the completed solve."""
+        self._check(self._L.lbm_mma_update(self._h, 1 if maximize else 0, float(move)))
+
+    def mma_update_with(self, grad, maximize: bool = True, move: float = 0.5):
+        """One MMA update with a caller's gradient (N float64, tensor or array)."""
+        import torch
+        if isinstance(grad, torch.Tensor):
+            g = grad.detach().to(torch.float64).contiguous().reshape(-1)
+            self._keep_grad = g
+            self._sync_in()
+        else:
+            g = np.ascontiguousarray(np.asarray(grad, dtype=np.float64).reshape(-1))
+        self._check(self._L.lbm_mma_update_with(self._h, _ptr(g), 1 if maximize else 0,
+                                                float(move)))
 
     def theta(self, out=None):
         """The handle's current theta (N float32) into ``out`` or a new device tensor."""

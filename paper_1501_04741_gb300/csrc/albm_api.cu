@@ -79,6 +79,9 @@ struct lbm_ctx {
   bool design_default = true;       // mask = FLUID nodes
   double* os_stats = nullptr;       // objective record of the current state (2 doubles)
   float* theta_saved = nullptr;     // continuous design during a threshold scan
+  // MMA history: x^{k-1}, x^{k-2}, last asymptotes (FP32, N each)
+  float* mma_hist = nullptr;
+  int mma_k = -1;                   // -1: lbm_mma_reset not called
   std::string err;
 };
 
@@ -284,6 +287,51 @@ __global__ void __launch_bounds__(256) threshold_kernel(long long N, const float
   if (i >= N) return;
   const float t = src[i];
   dst[i] = design[i] ? ((1.0f - t < eta) ? 1.0f : 0.0f) : t;
+}
+
+// One MMA iteration per design node (Svanberg's method, box 0..1, no other
+// constraints; the steps and constants of lbm_mma_update): asymptotes from
+// the last two changes, move limits, and the minimiser of the convex
+// separable approximation.  FP32; sign = -1 turns a maximised J into f = -J.
+__global__ void __launch_bounds__(256) mma_update_kernel(long long N, float* __restrict__ theta,
+                                                         float* __restrict__ x1,
+                                                         float* __restrict__ x2,
+                                                         float* __restrict__ Lh,
+                                                         float* __restrict__ Uh,
+                                                         const double* __restrict__ grad,
+                                                         const uint8_t* __restrict__ design,
+                                                         int k, float sign, float move) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N || !design[i]) return;
+  const float x = theta[i];
+  const float g = sign * (float)grad[i];
+  float l, u;
+  if (k < 2) {
+    l = x - 0.5f;
+    u = x + 0.5f;
+  } else {
+    const float xa = x1[i], xb = x2[i];
+    const float d1 = x - xa, d2 = xa - xb;   // exact signs (differences of FP32 values)
+    float gamma = 1.0f;
+    if ((d1 > 0.0f && d2 < 0.0f) || (d1 < 0.0f && d2 > 0.0f)) gamma = 0.7f;
+    else if ((d1 > 0.0f && d2 > 0.0f) || (d1 < 0.0f && d2 < 0.0f)) gamma = 1.2f;
+    const float dl = fminf(fmaxf(gamma * (xa - Lh[i]), 0.01f), 10.0f);
+    const float du = fminf(fmaxf(gamma * (Uh[i] - xa), 0.01f), 10.0f);
+    l = x - dl;
+    u = x + du;
+  }
+  const float alpha = fmaxf(fmaxf(0.0f, l + 0.1f * (x - l)), x - move);
+  const float beta = fminf(fminf(1.0f, u - 0.1f * (u - x)), x + move);
+  const float gp = fmaxf(g, 0.0f), gm = fmaxf(-g, 0.0f);
+  const float p = (u - x) * (u - x) * (1.001f * gp + 0.001f * gm + 1e-5f);
+  const float q = (x - l) * (x - l) * (0.001f * gp + 1.001f * gm + 1e-5f);
+  const float sp = sqrtf(p), sq = sqrtf(q);
+  const float y = (sp * l + sq * u) / (sp + sq);
+  x2[i] = x1[i];
+  x1[i] = x;
+  Lh[i] = l;
+  Uh[i] = u;
+  theta[i] = fminf(fmaxf(y, alpha), beta);
 }
 
 // default design mask: FLUID nodes
@@ -644,6 +692,7 @@ void lbm_destroy(lbm_handle h) {
   cudaFree(h->design);
   cudaFree(h->os_stats);
   cudaFree(h->theta_saved);
+  cudaFree(h->mma_hist);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->t0) cudaEventDestroy(h->t0);
   if (h->t1) cudaEventDestroy(h->t1);
@@ -1329,6 +1378,57 @@ lbm_status lbm_threshold_apply(lbm_handle h, double eta) {
   h->launches_other++;
   CK(h, cudaGetLastError());
   return do_reset(h);
+}
+
+lbm_status lbm_mma_reset(lbm_handle h) {
+  if (!h) return LBM_ERR_ARG;
+  lbm_status s = ensure_design(h);
+  if (s) return s;
+  if (!h->mma_hist) CK(h, cudaMalloc(&h->mma_hist, 4 * sizeof(float) * (size_t)h->N));
+  h->mma_k = 0;
+  return LBM_OK;
+}
+
+static lbm_status mma_launch(lbm_ctx* h, const double* grad, int maximize, double move) {
+  if (h->mma_k < 0) FAIL(h, LBM_ERR_STATE, "MMA not started (lbm_mma_reset)");
+  if (h->oneshot) FAIL(h, LBM_ERR_STATE, "a one-shot run is active");
+  if (!(move > 0.0 && move <= 1.0)) FAIL(h, LBM_ERR_ARG, "MMA move limit must be in (0, 1]");
+  float* hb = h->mma_hist;
+  const size_t n = (size_t)h->N;
+  albm::mma_update_kernel<<<node_blocks(h), 256, 0, h->stream>>>(
+      h->N, h->theta, hb, hb + n, hb + 2 * n, hb + 3 * n, grad, h->design, h->mma_k,
+      maximize ? -1.0f : 1.0f, (float)move);
+  h->launches_other++;
+  CK(h, cudaGetLastError());
+  h->mma_k++;
+  return LBM_OK;
+}
+
+lbm_status lbm_mma_update(lbm_handle h, int maximize, double move) {
+  if (!h) return LBM_ERR_ARG;
+  if (h->oneshot || h->t_adj != 0)
+    FAIL(h, LBM_ERR_STATE, "MMA needs a completed adjoint (lbm_run) before the update");
+  lbm_status s = mma_launch(h, h->grad, maximize, move);
+  if (s) return s;
+  return do_reset(h);
+}
+
+lbm_status lbm_mma_update_with(lbm_handle h, const double* grad, int maximize, double move) {
+  if (!h || !grad) return LBM_ERR_ARG;
+  const double* g = grad;
+  double* tmp = nullptr;
+  if (!is_device_ptr(grad)) {
+    CK(h, cudaMalloc(&tmp, sizeof(double) * (size_t)h->N));
+    CK(h, cudaMemcpyAsync(tmp, grad, sizeof(double) * (size_t)h->N, cudaMemcpyHostToDevice,
+                          h->stream));
+    g = tmp;
+  }
+  lbm_status s = mma_launch(h, g, maximize, move);
+  if (tmp) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+  }
+  return s;
 }
 
 lbm_status lbm_get_theta(lbm_handle h, float* dst) {

@@ -1,4 +1,5 @@
-"""One-shot topology optimisation (Sec. 3.3) driven through the C library.
+"""The optimisers of Sec. 3.3 driven through the C library: the one-shot
+descent and MMA.
 
 The loop of Sec. 3.3 -- one primal step, one adjoint (ALBS) step and one
 design update per iteration, Eq. gradient:update -- runs entirely in
@@ -12,6 +13,10 @@ libalbm (``lbm_oneshot_step``).  This module only schedules it:
 * at the end the threshold scan of Sec. 3.2 evaluates the binarised design
   for each level eta and the best level is applied (``lbm_threshold_scan``,
   ``lbm_threshold_apply``).
+
+``mma`` runs the other optimiser of Sec. 3.3: a full solve per design
+iteration (``lbm_run``) and one Method-of-Moving-Asymptotes update
+(``lbm_mma_update``).
 """
 from __future__ import annotations
 
@@ -65,3 +70,28 @@ def one_shot(P: Problem, theta0, iters: int, zeta: float, *, maximize: bool = Tr
         s.threshold_apply(etas[pick])
         theta_bin = s.theta().cpu().numpy()
         return OneShotResult(theta, history, etas, scan, etas[pick], scan[pick], theta_bin)
+
+
+@dataclasses.dataclass
+class MMAResult:
+    theta: np.ndarray        # design after the last update (float32, N)
+    history: list            # J of each design iteration's solve
+
+
+def mma(P: Problem, theta0, iters: int, *, maximize: bool = True, move: float = 0.5,
+        design=None, stream=None) -> MMAResult:
+    """The MMA design loop of Sec. 3.3: per iteration a full solve (primal,
+    unsteady adjoint, dJ/dtheta) and one MMA update of theta, all in the
+    library (``lbm_run``, ``lbm_mma_update``)."""
+    with Solver(P, theta0, stream=stream) as s:
+        s.set_design(design)
+        s.mma_reset()
+        hist = []
+        for _ in range(int(iters)):
+            s.run()
+            J = s.objective()
+            if not np.isfinite(J):
+                raise FloatingPointError(f"MMA objective became {J} at iteration {len(hist)}")
+            hist.append(J)
+            s.mma_update(maximize, move)
+        return MMAResult(s.theta().cpu().numpy(), hist)
