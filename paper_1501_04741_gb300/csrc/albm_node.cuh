@@ -56,6 +56,11 @@ __host__ __device__ inline int obj_kind(bool active, int objective) {
 #ifndef ALBM_MRT_FULL
 #define ALBM_MRT_FULL 0
 #endif
+// adjoint: the weighted moments C of c summed over the populations instead
+// of derived from A and the MRT moments (same values up to rounding)
+#ifndef ALBM_C_LOOP
+#define ALBM_C_LOOP 0
+#endif
 
 // Constants of one problem, passed by value to every kernel.
 struct KParams {
@@ -134,6 +139,14 @@ struct NodeOps {
   // a symmetric operator needing 9 (D3Q19) or 5 (D2Q9) moments, not 19 / 9.
   // P.mrt_r[k] holds c_k and P.mrt_diag holds 1 - s (set by fill_mrt).
   __device__ static __forceinline__ void mrt_op(const KParams& P, const float* x, float* y) {
+    float m[L::NMOM];
+    mrt_op_m(P, x, y, m);
+  }
+
+  // mrt_op that also returns m[k] = c_k (U_k . x) for the stress and
+  // conserved moments (the rank-one weights; other entries unset)
+  __device__ static __forceinline__ void mrt_op_m(const KParams& P, const float* x, float* y,
+                                                  float* m) {
 #if ALBM_MRT_FULL
     // the same operator through all moments: y = sum_k r_k U_k (U_k . x)
     float mf[L::NMOM];
@@ -158,7 +171,6 @@ struct NodeOps {
     }
     return;
 #endif
-    float m[L::NMOM];
 #pragma unroll
     for (int k = 0; k < L::NMOM; ++k) {
       m[k] = 0.0f;
@@ -176,6 +188,29 @@ struct NodeOps {
         if ((L::stress(k) || L::conserved(k)) && L::U(k, i) != 0) v += float(L::U(k, i)) * m[k];
       y[i] = v;
     }
+  }
+
+  // Weighted moments of the rows of U, sum_i w_i U(k,i) (e_ia (e_ib)), from
+  // the weights times 36 (integers for D2Q9 and D3Q19), so that the entries
+  // that vanish by symmetry are exact zeros and drop out at compile time.
+  __host__ __device__ static constexpr int w36(int i) { return int(L::w(i) * 36.0f + 0.5f); }
+  __host__ __device__ static constexpr int ecomp(int i, int a) {
+    return a == 0 ? L::ex(i) : (a == 1 ? L::ey(i) : L::ez(i));
+  }
+  __host__ __device__ static constexpr int UW0(int k) {
+    int s = 0;
+    for (int i = 0; i < Q; ++i) s += w36(i) * L::U(k, i);
+    return s;
+  }
+  __host__ __device__ static constexpr int UW1(int k, int a) {
+    int s = 0;
+    for (int i = 0; i < Q; ++i) s += w36(i) * ecomp(i, a) * L::U(k, i);
+    return s;
+  }
+  __host__ __device__ static constexpr int UW2(int k, int a, int b) {
+    int s = 0;
+    for (int i = 0; i < Q; ++i) s += w36(i) * ecomp(i, a) * ecomp(i, b) * L::U(k, i);
+    return s;
   }
 
   __host__ __device__ static constexpr int Dsq(int k) {
@@ -608,40 +643,85 @@ struct NodeOps {
       }
     }
     // ---- fluid collision ----
-    float c[Q];
+    // c = (d W / d f_noneq)^T a: (1 - omega) a for BGK; the symmetric MRT
+    // operator diag a + sum_k U_k m_k (stress and conserved moments k)
+    float c[Q], mk[L::NMOM];
     if (MRT) {
-      mrt_op(P, a, c);
+      mrt_op_m(P, a, c, mk);
     } else {
 #pragma unroll
       for (int i = 0; i < Q; ++i) c[i] = P.one_m_omega * a[i];
     }
+    // weighted moments A of a and C of c (0th, 1st, 2nd order in e)
     float A0 = 0.0f, A1[3] = {0.0f, 0.0f, 0.0f}, A2[3][3];
-    float C0 = 0.0f, C1[3] = {0.0f, 0.0f, 0.0f}, C2[3][3];
+    float C0, C1[3], C2[3][3];
 #pragma unroll
     for (int p_ = 0; p_ < 3; ++p_)
 #pragma unroll
-      for (int q_ = 0; q_ < 3; ++q_) {
-        A2[p_][q_] = 0.0f;
-        C2[p_][q_] = 0.0f;
-      }
+      for (int q_ = 0; q_ < 3; ++q_) A2[p_][q_] = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
       const float aw = a[i] * L::w(i);
-      const float cw = c[i] * L::w(i);
       A0 += aw;
-      C0 += cw;
 #pragma unroll
       for (int p_ = 0; p_ < 3; ++p_) {
         if (e[p_]) {
           A1[p_] += float(e[p_]) * aw;
-          C1[p_] += float(e[p_]) * cw;
 #pragma unroll
-          for (int q_ = p_; q_ < 3; ++q_) {
-            if (e[q_]) {
-              A2[p_][q_] += float(e[p_] * e[q_]) * aw;
-              C2[p_][q_] += float(e[p_] * e[q_]) * cw;
-            }
+          for (int q_ = p_; q_ < 3; ++q_)
+            if (e[q_]) A2[p_][q_] += float(e[p_] * e[q_]) * aw;
+        }
+      }
+    }
+#if ALBM_MRT_FULL || ALBM_C_LOOP
+    if (MRT || ALBM_C_LOOP) {
+      C0 = 0.0f;
+#pragma unroll
+      for (int p_ = 0; p_ < 3; ++p_) {
+        C1[p_] = 0.0f;
+#pragma unroll
+        for (int q_ = 0; q_ < 3; ++q_) C2[p_][q_] = 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
+        const float cw = c[i] * L::w(i);
+        C0 += cw;
+#pragma unroll
+        for (int p_ = 0; p_ < 3; ++p_) {
+          if (e[p_]) {
+            C1[p_] += float(e[p_]) * cw;
+#pragma unroll
+            for (int q_ = p_; q_ < 3; ++q_)
+              if (e[q_]) C2[p_][q_] += float(e[p_] * e[q_]) * cw;
+          }
+        }
+      }
+    } else
+#endif
+    {
+      // C = diag A + sum_k m_k (weighted moments of U_k): the moments of the
+      // rows of U are compile-time constants, mostly zero by symmetry
+      const float diag = MRT ? P.mrt_diag : P.one_m_omega;
+      C0 = diag * A0;
+#pragma unroll
+      for (int p_ = 0; p_ < 3; ++p_) {
+        C1[p_] = diag * A1[p_];
+#pragma unroll
+        for (int q_ = p_; q_ < 3; ++q_) C2[p_][q_] = diag * A2[p_][q_];
+      }
+      if (MRT) {
+#pragma unroll
+        for (int k = 0; k < L::NMOM; ++k) {
+          if (!(L::stress(k) || L::conserved(k))) continue;
+          if (UW0(k) != 0) C0 += float(UW0(k)) * (1.0f / 36.0f) * mk[k];
+#pragma unroll
+          for (int p_ = 0; p_ < L::DIM; ++p_) {
+            if (UW1(k, p_) != 0) C1[p_] += float(UW1(k, p_)) * (1.0f / 36.0f) * mk[k];
+#pragma unroll
+            for (int q_ = p_; q_ < L::DIM; ++q_)
+              if (UW2(k, p_, q_) != 0) C2[p_][q_] += float(UW2(k, p_, q_)) * (1.0f / 36.0f) * mk[k];
           }
         }
       }
