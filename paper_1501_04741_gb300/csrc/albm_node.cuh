@@ -61,6 +61,13 @@ __host__ __device__ inline int obj_kind(bool active, int objective) {
 #ifndef ALBM_C_LOOP
 #define ALBM_C_LOOP 0
 #endif
+// MRT: keep the conserved moments in the rank-one operator.  They act on
+// f - f_eq(rho, u), whose density and momentum vanish, and in the adjoint on
+// a vector that (I - d f_eq / d f)^T annihilates along them, so by default
+// only the stress moments are applied (results equal up to rounding).
+#ifndef ALBM_MRT_CONSERVED
+#define ALBM_MRT_CONSERVED 0
+#endif
 
 // Constants of one problem, passed by value to every kernel.
 struct KParams {
@@ -174,7 +181,7 @@ struct NodeOps {
 #pragma unroll
     for (int k = 0; k < L::NMOM; ++k) {
       m[k] = 0.0f;
-      if (!(L::stress(k) || L::conserved(k))) continue;
+      if (!rank_one(k)) continue;
 #pragma unroll
       for (int i = 0; i < Q; ++i)
         if (L::U(k, i) != 0) m[k] += float(L::U(k, i)) * x[i];
@@ -185,9 +192,14 @@ struct NodeOps {
       float v = P.mrt_diag * x[i];
 #pragma unroll
       for (int k = 0; k < L::NMOM; ++k)
-        if ((L::stress(k) || L::conserved(k)) && L::U(k, i) != 0) v += float(L::U(k, i)) * m[k];
+        if (rank_one(k) && L::U(k, i) != 0) v += float(L::U(k, i)) * m[k];
       y[i] = v;
     }
+  }
+
+  // moments carried by the rank-one terms of mrt_op
+  __host__ __device__ static constexpr bool rank_one(int k) {
+    return L::stress(k) || (ALBM_MRT_CONSERVED && L::conserved(k));
   }
 
   // Weighted moments of the rows of U, sum_i w_i U(k,i) (e_ia (e_ib)), from
@@ -714,7 +726,7 @@ struct NodeOps {
       if (MRT) {
 #pragma unroll
         for (int k = 0; k < L::NMOM; ++k) {
-          if (!(L::stress(k) || L::conserved(k))) continue;
+          if (!rank_one(k)) continue;
           if (UW0(k) != 0) C0 += float(UW0(k)) * (1.0f / 36.0f) * mk[k];
 #pragma unroll
           for (int p_ = 0; p_ < L::DIM; ++p_) {
