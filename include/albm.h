@@ -228,17 +228,23 @@ long long lbm_recompute_steps(lbm_handle h);
 
 /* Batched primal steps (continuous batching): advance each of
  * the n handles by up to k steps, one kernel launch per step covering every
- * handle that has not reached its horizon (at most 64 handles per launch;
- * larger batches are split).  The per-node arithmetic is that of
- * lbm_primal_step, so results are bit-identical to driving each handle
- * alone.  All handles must share lattice, collision, scalar count, storage
- * precision and stream.  Errors: LBM_ERR_ARG, LBM_ERR_STATE (an adjoint has
- * started on a handle), LBM_ERR_OOM. */
+ * handle below 2^20 nodes that has not reached its horizon (at most 64
+ * handles per launch; larger batches are split); a handle of 2^20 nodes or
+ * more fills the GPU alone and gets its own single-instance launch within
+ * the step.  The per-node arithmetic, and the grouping of the per-step
+ * objective sums, are those of lbm_primal_step, so results are
+ * bit-identical to driving each handle alone (16-bit storage with even nx,
+ * whose single-instance primal updates node pairs, groups its per-step
+ * objective sums differently: equal up to rounding).  All handles must
+ * share lattice, collision, scalar count, storage precision and stream.
+ * Errors: LBM_ERR_ARG, LBM_ERR_STATE (an adjoint has started on a handle),
+ * LBM_ERR_OOM. */
 lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k);
 
 /* Batched adjoint steps: each handle that has adjoint steps left goes back
  * up to k steps (Eq. adjoint:iteration), one launch per step for all of
- * them; states are restored per handle by its own checkpoint schedule.  A
+ * them (handles of 2^20 nodes or more: their own launch, as for the
+ * primal); states are restored per handle by its own checkpoint schedule.  A
  * handle whose adjoint has not started starts at its current primal time.
  * Same requirements and errors as lbm_batch_primal_step. */
 lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k);

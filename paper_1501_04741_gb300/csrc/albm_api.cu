@@ -887,6 +887,17 @@ static lbm_status batch_launch(lbm_ctx* h0, albm::BatchArgs& args, long long blo
   return LBM_OK;
 }
 
+// Instances at least this large fill the GPU alone: inside a batched step
+// they run their own single-instance launch (the same kernels as when they
+// are driven alone), and only the smaller ones share the batched launch.
+constexpr long long kBatchAloneNodes = 1LL << 20;
+
+struct BatchMove {
+  lbm_ctx* h;
+  int src, dst;
+  bool alone;
+};
+
 lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
   lbm_status st = batch_check(hs, n);
   if (st) return st;
@@ -896,7 +907,7 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
   for (int step = 0; step < k; ++step) {
     args.n = 0;
     long long blocks = 0;
-    std::vector<std::pair<lbm_ctx*, std::pair<int, int>>> moved;  // handle, (src, dst)
+    std::vector<BatchMove> moved;
     for (int i = 0; i < n; ++i) {
       lbm_ctx* h = hs[i];
       if (h->t >= h->p.nsteps) continue;  // horizon reached
@@ -904,6 +915,12 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
       int dst;
       lbm_status s = acquire_evict(h, h->t, &dst);
       if (s) return batch_fail(hs[0], h, s);
+      if (h->N >= kBatchAloneNodes) {
+        s = launch_primal(h, src, dst, h->t, true, K_PRIMAL);  // folds its own objective
+        if (s) return batch_fail(hs[0], h, s);
+        moved.push_back({h, src, dst, true});
+        continue;
+      }
       h->buf_time[dst] = -2;  // reserved until the launch is issued
       albm::InstanceDesc& D = args.inst[args.n++];
       memset(&D, 0, sizeof(D));
@@ -914,8 +931,10 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
       D.flags = h->flags;
       D.obj = h->c[h->t] != 0.0 ? h->partials : nullptr;
       D.block_begin = blocks;
-      blocks += (h->N + albm::kBlock - 1) / albm::kBlock;
-      moved.push_back({h, {src, dst}});
+      // blocks of the single-instance primal's size, so that the objective
+      // partials are grouped as when the instance runs alone
+      blocks += (h->N + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK;
+      moved.push_back({h, src, dst, false});
       if (args.n == albm::kMaxBatch) {
         s = batch_launch(hs[0], args, blocks, false);
         if (s) return s;
@@ -927,12 +946,12 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
       if (s) return s;
     }
     for (auto& m : moved) {
-      lbm_ctx* h = m.first;
-      if (h->c[h->t] != 0.0) {
-        lbm_status s = fold_objective(h, h->t, h->nblocks);
+      lbm_ctx* h = m.h;
+      if (!m.alone && h->c[h->t] != 0.0) {
+        lbm_status s = fold_objective(h, h->t, (h->N + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK);
         if (s) return batch_fail(hs[0], h, s);
       }
-      h->buf_time[m.second.second] = h->t + 1;
+      h->buf_time[m.dst] = h->t + 1;
       h->t += 1;
       if (h->t == h->p.nsteps) {
         lbm_status s = record_final_objective(h);
@@ -957,6 +976,7 @@ lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k) {
     args.n = 0;
     long long blocks = 0;
     std::vector<lbm_ctx*> moved;
+    bool any = false;
     for (int i = 0; i < n; ++i) {
       lbm_ctx* h = hs[i];
       if (h->t_adj <= 0) continue;  // adjoint finished
@@ -965,6 +985,13 @@ lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k) {
         if (h->buf_time[b] > nn) h->buf_time[b] = -1;
       lbm_status s = ensure_state(h, nn);
       if (s) return batch_fail(hs[0], h, s);
+      any = true;
+      if (h->N >= kBatchAloneNodes) {
+        s = launch_adjoint(h, nn, 1);  // flips its own adjoint buffers
+        if (s) return batch_fail(hs[0], h, s);
+        h->t_adj = nn;
+        continue;
+      }
       albm::InstanceDesc& D = args.inst[args.n++];
       memset(&D, 0, sizeof(D));
       D.P = h->kp;
@@ -995,7 +1022,7 @@ lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k) {
       h->lam_cur = 1 - h->lam_cur;
       h->t_adj -= 1;
     }
-    if (moved.empty()) break;
+    if (!any) break;
   }
   return LBM_OK;
 }

@@ -471,7 +471,7 @@ __device__ __forceinline__ int batch_instance(const BatchArgs& a) {
 }
 
 template <class L, int NS, bool MRT, class S>
-__global__ void __launch_bounds__(256, 4) primal_batch_kernel(const __grid_constant__ BatchArgs args) {
+__global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK, 1024 / ALBM_PRIMAL_BLOCK) primal_batch_kernel(const __grid_constant__ BatchArgs args) {
   const InstanceDesc& D = args.inst[batch_instance(args)];
   const int block = (int)((long long)blockIdx.x - D.block_begin);
   const long long idx = (long long)block * blockDim.x + threadIdx.x;
@@ -691,7 +691,7 @@ struct Launch {
     return cudaGetLastError();
   }
   static cudaError_t primal_batch(const BatchArgs& a, long long blocks, cudaStream_t st) {
-    primal_batch_kernel<L, NS, MRT, S><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+    primal_batch_kernel<L, NS, MRT, S><<<(unsigned)blocks, ALBM_PRIMAL_BLOCK, 0, st>>>(a);
     return cudaGetLastError();
   }
   static cudaError_t adjoint_batch(const BatchArgs& a, long long blocks, cudaStream_t st) {

@@ -59,6 +59,27 @@ def _batched(Ps, ths, **kw):
             s.close()
 
 
+def test_mixed_sizes_and_window_objective_equal_alone():
+    """One instance above 2^20 nodes (its own launch inside the batched step)
+    beside small ones (the shared launch), with an objective recorded over a
+    window of steps (per-step sums folded from block partials): J and
+    dJ/dtheta bit-identical to each instance driven alone."""
+    big = inputs.channel2d(dims=(1040, 1024, 1), design=(260, 780, 256, 768, 0, 1), nsteps=12,
+                           force=(1e-4, 0, 0), obj_window=5)
+    assert big.n_nodes >= 1 << 20
+    Ps = [big,
+          inputs.channel2d(dims=(42, 18, 1), design=(10, 30, 4, 14, 0, 1), nsteps=12,
+                           force=(1e-4, 0, 0), obj_window=4),
+          inputs.channel2d(dims=(60, 20, 1), design=(15, 45, 5, 15, 0, 1), nsteps=9,
+                           force=(1e-4, 0, 0), obj_window=4)]
+    ths = [inputs.theta_uniform(P, i + 7) for i, P in enumerate(Ps)]
+    Js, gs = _batched(Ps, ths)
+    for P, th, J, g in zip(Ps, ths, Js, gs):
+        J1, g1 = _alone(P, th)
+        assert J == J1, (P.dims, J, J1)
+        assert np.array_equal(g, g1), P.dims
+
+
 @pytest.mark.parametrize("family", ["2d", "3d"])
 def test_batched_equals_alone(family):
     Ps = _family_2d(7) if family == "2d" else _family_3d(5)
