@@ -219,3 +219,22 @@ def test_mma_closed_form_with_swapped_asymptotes_is_caught(monkeypatch):
     monkeypatch.setattr(M, "subproblem", bad)
     with pytest.raises(AssertionError):
         TM.test_subproblem_minimiser_matches_grid_search()
+
+
+def test_wrong_power_law_exponent_is_caught(monkeypatch):
+    orig = om.Model.G
+
+    def bad(self, theta):
+        if self.P.porosity == "power":
+            return 1 - theta ** (self.P.porosity_q - 1)
+        return orig(self, theta)
+    _mutate(monkeypatch, "G", bad)
+    with pytest.raises(AssertionError):
+        TP.test_porosity_law_at_intermediate_theta("power", 3.0, 0.6)
+
+
+def test_swapped_diffusivity_interpolation_is_caught(monkeypatch):
+    _mutate(monkeypatch, "alpha",
+            lambda self, theta: theta * self.P.alpha_fluid + (1 - theta) * self.P.alpha_solid)
+    with pytest.raises(AssertionError):
+        TP.test_scalar_diffusivity_interpolates_in_theta(0.3)

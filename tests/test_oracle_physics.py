@@ -215,6 +215,57 @@ def test_porosity_limits():
     assert j[:, solid].abs().max() < 1e-16
 
 
+@pytest.mark.parametrize("law,q", [("linear", 1.0), ("power", 3.0), ("ramp", 2.0)])
+@pytest.mark.parametrize("c", [0.25, 0.6])
+def test_porosity_law_at_intermediate_theta(law, q, c):
+    # Sec. 3.2: u_post = G(theta) u_pre.  An equilibrium state at uniform
+    # velocity U in a periodic box with uniform theta = c and no force
+    # collides to f_eq(rho, G(c) U), so its momentum is rho G(c) U exactly;
+    # G by the readings of the laws: 1 - c, 1 - c^q, (1 - c) / (1 + q c).
+    for coll in ("BGK", "MRT"):
+        P = inputs.Problem(lattice="D3Q19", dims=(6, 5, 4), walls="", collision=coll, tau=0.7,
+                           porosity=law, porosity_q=q, objective="none")
+        o = Oracle(P, np.full((4, 5, 6), c, np.float32))
+        U = (0.03, -0.02, 0.01)
+        m = o.model
+        n = o.n
+        u = torch.tensor(U, dtype=torch.float64)[:, None].expand(3, n)
+        F = m.feq(torch.ones(n, dtype=torch.float64), u).view(m.Q, *o.shape)
+        post = o.collide(F).reshape(m.Q, -1)
+        j = m.E.T @ post
+        # theta is held in FP32: evaluate G on the stored value
+        cf = float(np.float32(c))
+        Gf = {"linear": 1 - cf, "power": 1 - cf ** q, "ramp": (1 - cf) / (1 + q * cf)}[law]
+        want = Gf * torch.tensor(U, dtype=torch.float64)
+        assert (j - want[:, None]).abs().max() < 1e-15, (law, coll, c)
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.3, 1.0])
+def test_scalar_diffusivity_interpolates_in_theta(theta):
+    # Sec. 3.2: alpha = (1 - theta) alpha_fluid + theta alpha_solid; a Fourier
+    # mode of a pure-diffusion field in a box of uniform theta decays at
+    # alpha(theta) k^2 (up to O(k^2) lattice corrections).
+    L, a_f, a_s = 32, 0.05, 0.15
+    P = inputs.Problem(lattice="D3Q19", dims=(L, 2, 2), walls="", nscalars=1,
+                       alpha_fluid=a_f, alpha_solid=a_s, objective="none")
+    th = float(np.float32(theta))
+    o = Oracle(P, np.full((2, 2, L), theta, np.float32))
+    alpha = (1 - th) * a_f + th * a_s
+    m = o.model
+    F = o.initial().clone()
+    k = 2 * math.pi / L
+    x = torch.arange(L, dtype=torch.float64)
+    F[m.Q:] = (m.ws[:, None] * (0.5 + 0.1 * torch.sin(k * x))[None, :]).view(m.Qs, 1, 1, L)
+    nsteps = 200
+    with torch.no_grad():
+        for _ in range(nsteps):
+            F = o.step(F)
+    T = F[m.Q:].sum(0)[0, 0]
+    amp = float(((T - 0.5) * torch.sin(k * x)).sum() * 2 / L)
+    rate = -math.log(amp / 0.1) / nsteps
+    assert abs(rate - alpha * k * k) / (alpha * k * k) < 0.02
+
+
 def test_scalar_diffusion_decay_and_conservation():
     # Pure diffusion (u = 0, periodic): sum T is conserved and a Fourier mode
     # decays at rate alpha k^2 up to O(k^2) lattice corrections.
