@@ -172,6 +172,28 @@ def test_flags_channel_geometry():
     assert (fl[1:-1, 1:-1, 1:-1] == FLUID).all()
 
 
+def test_wall_and_hot_nodes_after_collision():
+    # Walls: full bounce-back of fluid and scalar populations; the hot patch
+    # is a wall for the fluid and holds the scalar at the rest equilibrium
+    # of T_hot (Dirichlet).
+    P = inputs.scaled(inputs.exchanger3d(), (14, 8, 8), T_hot=0.8)
+    o = Oracle(P, np.zeros(P.dims[::-1], np.float32))
+    F = _rand_state(o, 9, scale=0.02)
+    m = o.model
+    pre = F.reshape(m.M, -1)
+    post = o.collide(F).reshape(m.M, -1)
+    opp = torch.tensor([int(v) for v in m.fl.opp])
+    opps = torch.tensor([int(v) for v in m.sl.opp])
+    wall = o.flags == WALL
+    hot = o.flags == HOT
+    assert int(hot.sum()) > 0 and int(wall.sum()) > 0
+    for sel in (wall, hot):
+        assert torch.equal(post[:m.Q][:, sel], pre[:m.Q][opp][:, sel])
+    assert torch.equal(post[m.Q:][:, wall], pre[m.Q:][opps][:, wall])
+    want = torch.as_tensor(np.asarray(m.sl.w, dtype=np.float64) * 0.8)[:, None]
+    assert (post[m.Q:][:, hot] - want).abs().max() < 1e-15
+
+
 def test_zou_he_prescribed_values_after_collision():
     # Zou & He (Sec. 3): after the node operator the inlet node carries
     # u = u_in and the outlet node rho = rho_out.
