@@ -177,3 +177,30 @@ def test_driver_runs_schedule_and_scan():
     solid = (np.float32(1.0) - r.theta) < np.float32(r.best_eta)
     want = np.where(m, np.where(solid, np.float32(1.0), np.float32(0.0)), r.theta)
     assert np.array_equal(r.theta_binary, want)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_oneshot_with_16bit_storage(precision):
+    """The one-shot iteration with 16-bit states (even nx: the paired primal
+    kernel, and for the variance objective its per-step outlet mean) follows
+    the FP32 run: design change within the reduced-precision bounds of the
+    unsteady solve (gradients 0.6 BF16 / 0.1 FP16 relative), J within 1e-1 /
+    1e-2."""
+    P, K, zeta, pen, mx = CASES["mixer3d_variance"]
+    P = P.replace(dims=(10, 11, 10))
+    th0 = _band(P, 0)
+    mask = inputs.design_mask(P)
+    out = {}
+    for prec in ("fp32", precision):
+        with Solver(P.replace(precision=prec), torch.from_numpy(th0.reshape(-1)).cuda()) as s:
+            s.set_design(mask)
+            s.oneshot_reset()
+            s.oneshot_step(K, zeta, pen, mx)
+            J, Pv = s.oneshot_eval()
+            out[prec] = (_np(s.theta()) - th0.reshape(-1), J)
+    d32, J32 = out["fp32"]
+    d16, J16 = out[precision]
+    gb, jb = (0.6, 1e-1) if precision == "bf16" else (0.1, 1e-2)
+    assert np.isfinite(d16).all() and np.isfinite(J16)
+    assert _rel(d16, d32) <= gb, _rel(d16, d32)
+    assert abs(J16 - J32) <= jb * abs(J32), (J16, J32)
