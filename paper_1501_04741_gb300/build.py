@@ -24,7 +24,7 @@ OBJ_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIB_DIR, "libalbm.so")
 
-UNITS = ["albm_api.cu", "kern_d2q9.cu",
+UNITS = ["albm_api.cu", "kern_d2q9_f32.cu", "kern_d2q9_bf16.cu", "kern_d2q9_f16.cu",
          "kern_d3q19_mrt_f32.cu", "kern_d3q19_mrt_bf16.cu", "kern_d3q19_mrt_f16.cu",
          "kern_d3q19_bgk_f32.cu", "kern_d3q19_bgk_bf16.cu", "kern_d3q19_bgk_f16.cu",
          "albm_noalloc.cu"]

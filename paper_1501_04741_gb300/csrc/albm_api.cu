@@ -540,7 +540,7 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   h->N = (long long)p.nx * p.ny * p.nz;
   h->stream = (cudaStream_t)stream;
   bool ok = p.lattice == LBM_D2Q9
-                ? albm::kernels_d2q9(p.collision, p.nscalars, p.precision, &h->ks)
+                ? albm::kernels_d2q9(p.collision == LBM_MRT, p.nscalars, p.precision, &h->ks)
                 : albm::kernels_d3q19(p.collision == LBM_MRT, p.nscalars, p.precision, &h->ks);
   if (!ok) {
     *out = h;

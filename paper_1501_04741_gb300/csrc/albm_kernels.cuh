@@ -788,14 +788,25 @@ bool pick_scalars(int nscalars, KernelSet* out) {
 }
 
 // Lookup of the instantiated sets, defined in the per-lattice translation
-// units (the D3Q19 ones split by storage type so that they build in parallel).
-bool kernels_d2q9(int collision, int nscalars, int precision, KernelSet* out);
+// units (split by storage type so that they build in parallel).
+bool kernels_d2q9_f32(bool mrt, int nscalars, KernelSet* out);
+bool kernels_d2q9_bf16(bool mrt, int nscalars, KernelSet* out);
+bool kernels_d2q9_f16(bool mrt, int nscalars, KernelSet* out);
 bool kernels_d3q19_bgk_f32(int nscalars, KernelSet* out);
 bool kernels_d3q19_bgk_bf16(int nscalars, KernelSet* out);
 bool kernels_d3q19_bgk_f16(int nscalars, KernelSet* out);
 bool kernels_d3q19_mrt_f32(int nscalars, KernelSet* out);
 bool kernels_d3q19_mrt_bf16(int nscalars, KernelSet* out);
 bool kernels_d3q19_mrt_f16(int nscalars, KernelSet* out);
+
+inline bool kernels_d2q9(bool mrt, int nscalars, int precision, KernelSet* out) {
+  switch (precision) {
+    case 0: return kernels_d2q9_f32(mrt, nscalars, out);
+    case 1: return kernels_d2q9_bf16(mrt, nscalars, out);
+    case 2: return kernels_d2q9_f16(mrt, nscalars, out);
+    default: return false;
+  }
+}
 
 inline bool kernels_d3q19(bool mrt, int nscalars, int precision, KernelSet* out) {
   switch (precision) {

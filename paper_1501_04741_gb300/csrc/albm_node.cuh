@@ -25,6 +25,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <utility>
+
 #include "albm_lattice.cuh"
 
 namespace albm {
@@ -223,6 +225,32 @@ struct NodeOps {
     int s = 0;
     for (int i = 0; i < Q; ++i) s += w36(i) * ecomp(i, a) * ecomp(i, b) * L::U(k, i);
     return s;
+  }
+
+  // C += m_k (weighted moments of U_k) for one rank-one moment k; the
+  // weights are constant expressions, so zero terms vanish in the front end
+  template <int k>
+  __device__ static __forceinline__ void add_row_moment(float m, float& C0, float* C1,
+                                                        float (*C2)[3]) {
+    if constexpr (rank_one(k)) {
+      constexpr float s = 1.0f / 36.0f;
+      if constexpr (UW0(k) != 0) C0 += (float(UW0(k)) * s) * m;
+      if constexpr (UW1(k, 0) != 0) C1[0] += (float(UW1(k, 0)) * s) * m;
+      if constexpr (UW1(k, 1) != 0) C1[1] += (float(UW1(k, 1)) * s) * m;
+      if constexpr (UW1(k, 2) != 0) C1[2] += (float(UW1(k, 2)) * s) * m;
+      if constexpr (UW2(k, 0, 0) != 0) C2[0][0] += (float(UW2(k, 0, 0)) * s) * m;
+      if constexpr (UW2(k, 0, 1) != 0) C2[0][1] += (float(UW2(k, 0, 1)) * s) * m;
+      if constexpr (UW2(k, 0, 2) != 0) C2[0][2] += (float(UW2(k, 0, 2)) * s) * m;
+      if constexpr (UW2(k, 1, 1) != 0) C2[1][1] += (float(UW2(k, 1, 1)) * s) * m;
+      if constexpr (UW2(k, 1, 2) != 0) C2[1][2] += (float(UW2(k, 1, 2)) * s) * m;
+      if constexpr (UW2(k, 2, 2) != 0) C2[2][2] += (float(UW2(k, 2, 2)) * s) * m;
+    }
+  }
+  template <int... K>
+  __device__ static __forceinline__ void add_row_moments(std::integer_sequence<int, K...>,
+                                                         const float* mk, float& C0, float* C1,
+                                                         float (*C2)[3]) {
+    (add_row_moment<K>(mk[K], C0, C1, C2), ...);
   }
 
   __host__ __device__ static constexpr int Dsq(int k) {
@@ -723,20 +751,7 @@ struct NodeOps {
 #pragma unroll
         for (int q_ = p_; q_ < 3; ++q_) C2[p_][q_] = diag * A2[p_][q_];
       }
-      if (MRT) {
-#pragma unroll
-        for (int k = 0; k < L::NMOM; ++k) {
-          if (!rank_one(k)) continue;
-          if (UW0(k) != 0) C0 += float(UW0(k)) * (1.0f / 36.0f) * mk[k];
-#pragma unroll
-          for (int p_ = 0; p_ < L::DIM; ++p_) {
-            if (UW1(k, p_) != 0) C1[p_] += float(UW1(k, p_)) * (1.0f / 36.0f) * mk[k];
-#pragma unroll
-            for (int q_ = p_; q_ < L::DIM; ++q_)
-              if (UW2(k, p_, q_) != 0) C2[p_][q_] += float(UW2(k, p_, q_)) * (1.0f / 36.0f) * mk[k];
-          }
-        }
-      }
+      if (MRT) add_row_moments(std::make_integer_sequence<int, L::NMOM>{}, mk, C0, C1, C2);
     }
 #pragma unroll
     for (int p_ = 0; p_ < 3; ++p_)
