@@ -25,6 +25,10 @@ def _cases():
         "exchanger3d_bgk": exch,
         "exchanger3d_mrt_power": exch.replace(collision="MRT", porosity="power",
                                               porosity_q=3.0),
+        # the paper's channels: signed inlet with the mixing flux, heat flux alone
+        "paper_mixer_signed": inputs.scaled(inputs.paper_mixer_empty(), (10, 6, 6), nsteps=16),
+        "paper_exchanger_heatflux": inputs.scaled(inputs.paper_exchanger_empty(), (12, 6, 6),
+                                                  nsteps=16),
     }
 
 
