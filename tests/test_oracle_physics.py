@@ -426,3 +426,25 @@ def test_outlet_variance_of_a_two_level_profile():
     ys = o.y[out]
     p = float((ys >= half).double().mean())
     assert abs(float(o.F_obj(F)) - p * (1 - p)) < 1e-14
+
+
+def test_paper_presets_follow_the_printed_cases():
+    # inputs.paper_*_empty carry Tab. tab:cases: sizes, nu (tau = 3 nu + 1/2),
+    # the diffusivities and the design span (nodes x_first..x_last); the
+    # pressure drop is not an input (the inlet runs at its velocity limit).
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_table_cases.txt")
+    rows = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        c, *v = line.split()
+        rows[c] = [float(x) for x in v]
+    for case, P in (("mixer", inputs.paper_mixer_empty()), ("exchanger", inputs.paper_exchanger_empty())):
+        Lx, Ly, Lz, x0, x1, dp, nu, a_f, a_s = rows[case]
+        assert tuple(P.dims) == (int(Lx), int(Ly), int(Lz))
+        assert abs(P.tau - (3 * nu + 0.5)) < 1e-12
+        assert P.alpha_fluid == a_f and P.alpha_solid == a_s
+        assert P.design[0] == int(x0) and P.design[1] == int(x1) + 1
+        assert P.u_in == 0.05 and P.collision == "MRT" and P.nscalars == 1
+
