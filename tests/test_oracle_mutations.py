@@ -238,3 +238,31 @@ def test_swapped_diffusivity_interpolation_is_caught(monkeypatch):
             lambda self, theta: theta * self.P.alpha_fluid + (1 - theta) * self.P.alpha_solid)
     with pytest.raises(AssertionError):
         TP.test_scalar_diffusivity_interpolates_in_theta(0.3)
+
+
+def test_inverted_signed_inlet_is_caught(monkeypatch):
+    orig = om.Model.inlet_scalar
+
+    def bad(self, s, y):
+        c = orig(self, s, y)
+        return -c if self.P.scalar_inlet == "signed" else c     # -1 above, +1 below
+    _mutate(monkeypatch, "inlet_scalar", bad)
+    with pytest.raises(AssertionError):
+        TP.test_signed_inlet_values_after_collision()
+
+
+def test_heat_flux_with_the_pressure_term_is_caught(monkeypatch):
+    orig = om.Model.objective
+
+    def bad(self, F, theta, flags, y, n_inlet=1, n_outlet=1):
+        if self.P.objective == "heatflux":                     # pressure term kept
+            saved = self.P
+            self.P = saved.replace(objective="heatflux_dp")
+            try:
+                return orig(self, F, theta, flags, y, n_inlet, n_outlet)
+            finally:
+                self.P = saved
+        return orig(self, F, theta, flags, y, n_inlet, n_outlet)
+    _mutate(monkeypatch, "objective", bad)
+    with pytest.raises(AssertionError):
+        TP.test_heat_flux_pressure_drop_term()
