@@ -107,7 +107,8 @@ typedef struct {
   int nsteps;           /* horizon N of the unsteady problem                 */
   int precision;        /* lbm_precision of the stored populations           */
   int ckpt_every;       /* level-1 checkpoint stride (0 = automatic)         */
-  double mem_budget;    /* bytes for stored states (0 = automatic)           */
+  double mem_budget;    /* bytes for stored states (0 = 0.90 of the free
+                           device memory at lbm_create)                      */
   int kernel;           /* 0: automatic (one thread per node); 1: one thread
                            per node, gathers from global memory; 2 or 3:
                            tile-staged, x-row segments of 128-node tiles
