@@ -17,6 +17,11 @@ and the synthetic stand-ins derived from them:
 * ``exchanger3d`` - D3Q19 BGK + D3Q7 temperature heat exchanger 512x256x256,
   hot bottom patch T=1, inlet T=0, Pr=0.7; outlet heat flux minus 0.1 times
   the pressure drop (Sec. 4.2, Eq. "exchanger:obj").
+* ``paper_mixer_empty``, ``paper_exchanger_empty`` - the paper's own empty
+  channels (450x50x50 and 352x50x50, Tab. "tab:cases") for comparison with
+  its printed results.
+* ``batch_instances``, ``serving_requests`` - seeded families of instances
+  and timed requests for the batched and served forms.
 
 Porosity naming: ``theta`` is the solid fraction (0 = fluid, 1 = solid), i.e.
 ``theta = 1 - w`` with the paper's ``w`` of Sec. 3.2.
