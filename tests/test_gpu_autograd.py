@@ -32,7 +32,7 @@ def test_autograd_single_matches_oracle_and_fd():
             J = albm_objective(theta, s)
             (2.5 * J).backward()
         assert J.dtype == torch.float64
-        assert abs(J.item() - J_ref) <= 1e-4 * abs(J_ref)
+        assert abs(J.item() - J_ref) <= 5e-5 * abs(J_ref)
         g = theta.grad.double().cpu().numpy() / 2.5
         assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max() + 1e-6 * np.abs(g).max()
         for i in np.argsort(-np.abs(g_ref))[:2]:
@@ -57,7 +57,7 @@ def test_autograd_batch_mixed_families():
             o = Oracle(P, th)
             J_ref, g_ref, _ = o.gradient()
             g_ref = g_ref.reshape(-1).numpy()
-            assert abs(Js[k].item() - J_ref) <= 1e-4 * abs(J_ref)
+            assert abs(Js[k].item() - J_ref) <= 5e-5 * abs(J_ref)
             g = thetas[k].grad.double().cpu().numpy() / float(w[k])
             assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max()
         # batched and single autograd agree bit for bit

@@ -5,12 +5,19 @@ Tolerances (FP32 kernels against FP64):
 * one primal step from the same state: max |f_gpu - f_oracle| <= 2e-6 max|f|;
 * one adjoint step from the same state and lambda: <= 2e-5 of max|lambda|
   (and of max|dJ/dtheta| for the theta terms);
-* whole trajectories: populations within 1e-5 of max|f| after the stated
-  steps and dJ/dtheta within 1e-4 (inf-norm relative), the two bars the
-  problem statement fixes; J within 1e-4 relative.  J has no stated bar:
-  the dissipation objective is quadratic in f - f_eq, about 1e-3 of |f| at
-  these flow speeds, so a population error of 1e-5 |f| allows a relative J
-  error of order 2e-5 |f| / |f - f_eq|; J is gated like the gradient.
+* whole trajectories, the two bars the problem statement fixes:
+  - fluid populations within 1e-5 relative error element by element,
+    max_i |f_gpu,i - f_i| / |f_i| <= 1e-5 (every fluid population is
+    positive and near its weight w_i at these flow speeds);
+  - scalar populations, whose values cross zero (signed inlets) or start at
+    zero, within 1e-5 absolute; the scalar fields are bounded by their
+    boundary values (magnitude 1), so this is the same bar relative to the
+    field's range;
+  - dJ/dtheta within 1e-4 (inf-norm relative);
+  - J within 5e-5 relative.  J has no stated bar: the dissipation objective
+    is quadratic in f - f_eq, about 1e-3 of |f| at these flow speeds, so a
+    population error of 1e-5 |f| would allow a relative J error of order
+    2e-5 |f| / |f - f_eq|; measured errors are below 2.5e-5.
 Lattice sizes are odd so that the node count leaves a ragged last block.
 """
 import numpy as np
@@ -76,6 +83,19 @@ def _solver(P, theta, **kw):
 
 def _np(t):
     return t.detach().cpu().numpy().astype(np.float64)
+
+
+def assert_populations_close(f_gpu, f_ref, Q, label=""):
+    """The trajectory bar: fluid rows element by element within 1e-5
+    relative, scalar rows within 1e-5 absolute."""
+    rel = np.abs(f_gpu[:Q] - f_ref[:Q]) / np.abs(f_ref[:Q])
+    print(f"[parity] {label} fluid max rel {rel.max():.2e}", end="")
+    assert rel.max() <= 1e-5, rel.max()
+    if f_ref.shape[0] > Q:
+        ab = np.abs(f_gpu[Q:] - f_ref[Q:]).max()
+        print(f"  scalar max abs {ab:.2e}", end="")
+        assert ab <= 1e-5, ab
+    print()
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -145,8 +165,8 @@ def test_trajectory_objective_and_gradient(name):
         J_gpu = s.objective()
         s.adjoint_step(P.nsteps)
         grad = _np(s.gradient())
-    assert np.abs(f_gpu - fN).max() <= 1e-5 * np.abs(fN).max()
-    assert abs(J_gpu - J) <= 1e-4 * abs(J) + 1e-12
+    assert_populations_close(f_gpu, fN, o.model.Q, name)
+    assert abs(J_gpu - J) <= 5e-5 * abs(J) + 1e-12, (J_gpu, J)
     assert np.abs(grad - g).max() <= 1e-4 * np.abs(g).max()
 
 
@@ -188,8 +208,8 @@ def test_channel2d_full_config_parity():
         J_gpu = s.objective()
         s.adjoint_step(P.nsteps)
         grad = _np(s.gradient())
-    assert np.abs(f_gpu - fN).max() <= 1e-5 * np.abs(fN).max()
-    assert abs(J_gpu - J) <= 1e-4 * abs(J)
+    assert_populations_close(f_gpu, fN, 9, "channel2d full")
+    assert abs(J_gpu - J) <= 5e-5 * abs(J), (J_gpu, J)
     assert np.abs(grad - g).max() <= 1e-4 * np.abs(g).max()
     # and within 1e-3 of central differences of the FP64 objective
     for i in list(np.argsort(-np.abs(g))[:3]):

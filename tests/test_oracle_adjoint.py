@@ -72,6 +72,35 @@ def test_one_step_duality(name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
+def test_one_step_adjoint_against_forward_differences(name):
+    # The adjoint step against the forward map alone, without any automatic
+    # differentiation on the other side: <lambda, (SW(f + h df, theta + h
+    # dtheta) - SW(f - h df, theta - h dtheta)) / 2h> is the directional
+    # derivative <lambda, A df + B dtheta> up to O(h^2), and must equal
+    # <A^T lambda, df> + <B^T lambda, dtheta> from the adjoint step.  A
+    # dropped term, a wrong sign or a transposed index in the reverse
+    # product fails it.
+    P = CASES[name]
+    o = Oracle(P, _theta(P, 1))
+    F = _state(o, 2)
+    rng = np.random.default_rng(13)
+    lam = torch.tensor(rng.standard_normal(F.shape))
+    df = torch.tensor(rng.standard_normal(F.shape)) * 0.01
+    dth = torch.tensor(rng.standard_normal(o.n)) * 0.1
+    h = 1e-5
+    lamF, lamth = o.adjoint_step(lam, F)
+    # the population and the theta directions separately, so that a small
+    # theta term cannot hide behind the population term
+    for a, b, rhs in ((df, 0 * dth, float((lamF * df).sum())),
+                      (0 * df, dth, float((lamth * dth).sum()))):
+        with torch.no_grad():
+            up = o.step(F + h * a, o.theta + h * b)
+            dn = o.step(F - h * a, o.theta - h * b)
+        lhs = float((lam * (up - dn)).sum()) / (2 * h)
+        assert abs(lhs - rhs) <= 1e-6 * max(abs(rhs), 1e-4), (lhs, rhs)
+
+
+@pytest.mark.parametrize("name", list(CASES))
 def test_gradient_matches_central_differences(name):
     P = CASES[name]
     o = Oracle(P, _theta(P, 4))

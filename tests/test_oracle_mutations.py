@@ -266,3 +266,51 @@ def test_heat_flux_with_the_pressure_term_is_caught(monkeypatch):
     _mutate(monkeypatch, "objective", bad)
     with pytest.raises(AssertionError):
         TP.test_heat_flux_pressure_drop_term()
+
+
+def _window_weights(extra: int, scale_extra: int):
+    """Window weights with `extra` more terms and weight 1/(K + scale_extra)."""
+    def weights_for(N, K):
+        c = np.zeros(N + 1)
+        if K <= 0:
+            c[N] = 1.0
+        else:
+            c[max(N - K + 1 - extra, 0):] = 1.0 / (K + scale_extra)
+        return c
+    return weights_for
+
+
+@pytest.mark.parametrize("extra,scale_extra", [(1, 0), (0, 1), (1, 1)])
+def test_window_off_by_one_is_caught(monkeypatch, extra, scale_extra):
+    import oracle.solver as osv
+    wf = _window_weights(extra, scale_extra)
+    monkeypatch.setattr(om.Model, "weights",
+                        lambda self: wf(int(self.P.nsteps), int(self.P.obj_window)))
+    with pytest.raises(AssertionError):
+        TP.test_window_objective_is_the_mean_of_the_last_K_steps("D2Q9", (6, 5, 1), 7, 3)
+    monkeypatch.undo()
+    monkeypatch.setattr(osv, "_weights", lambda P, N: wf(N, int(P.obj_window)))
+    with pytest.raises(AssertionError):
+        TP.test_window_objective_is_the_mean_of_the_last_K_steps("D3Q19", (4, 3, 5), 7, 3)
+
+
+def test_outlet_scalar_taken_as_plain_sum_is_caught(monkeypatch):
+    def naive(self, g, v):
+        return g, g.sum(0)             # T* = sum g, unknowns left as they came in
+    _mutate(monkeypatch, "scalar_outlet", naive)
+    for lat in ("D2Q9", "D3Q19"):
+        with pytest.raises(AssertionError):
+            TP.test_outlet_scalar_reconstruction_worked_example(lat)
+
+
+def test_outlet_scalar_with_pre_collision_sign_is_caught(monkeypatch):
+    # unknowns at equilibrium with the velocity reversed (e.v taken with the
+    # outward instead of the streaming direction)
+    orig = om.Model.scalar_outlet
+
+    def bad(self, g, v):
+        return orig(self, g, -v)
+    _mutate(monkeypatch, "scalar_outlet", bad)
+    for lat in ("D2Q9", "D3Q19"):
+        with pytest.raises(AssertionError):
+            TP.test_outlet_scalar_reconstruction_worked_example(lat)

@@ -448,3 +448,107 @@ def test_paper_presets_follow_the_printed_cases():
         assert P.design[0] == int(x0) and P.design[1] == int(x1) + 1
         assert P.u_in == 0.05 and P.collision == "MRT" and P.nscalars == 1
 
+
+
+# ---------------------------------------------------------------------------
+# time weights of the window objective, outlet scalar reconstruction
+# ---------------------------------------------------------------------------
+
+def _ghost_mode(lattice, dims, tau, eps):
+    """A spatially uniform non-equilibrium state of a fully periodic box:
+    f_i = w_i (1 + eps (e_ix^2 - e_iy^2)).  The perturbation carries no
+    mass and no momentum, so rho = 1 and u = 0 at every node; streaming a
+    uniform field changes nothing, and BGK without force or porosity scales
+    f - f_eq by (1 - omega) per step.  Hence f^n - f_eq = (1 - omega)^n
+    (f^0 - f_eq) exactly, and the stress Pi_ab = sum_i e_ia e_ib (f_i - f_eq,i)
+    is diag(2/9, -2/9, 0) eps (1 - omega)^n on D2Q9 and D3Q19 (sum w e_x^4 =
+    1/3, sum w e_x^2 e_y^2 = 1/9 on both).  The dissipation 2 rho nu S:S with
+    S = -(3 omega / 2) Pi is then (4/9) nu omega^2 eps^2 (1 - omega)^(2n) per
+    node."""
+    P = inputs.Problem(lattice=lattice, dims=dims, collision="BGK", tau=tau, walls="",
+                       channel="periodic", objective="dissipation")
+    o = Oracle(P, np.zeros(dims[::-1], np.float32))
+    m = o.model
+    E = m.E.numpy()
+    h = torch.tensor(E[:, 0] ** 2 - E[:, 1] ** 2, dtype=torch.float64)
+    F = (m.w * (1 + eps * h))[:, None].expand(m.Q, o.n).clone().view(m.Q, *o.shape)
+    omega = 1.0 / tau
+    nu = (tau - 0.5) / 3.0
+    F0 = o.n * 4.0 / 9.0 * nu * omega ** 2 * eps ** 2
+
+    def closed(n):
+        return F0 * (1.0 - omega) ** (2 * n)
+    return P, o, F, closed
+
+
+@pytest.mark.parametrize("lattice,dims", [("D2Q9", (6, 5, 1)), ("D3Q19", (4, 3, 5))])
+@pytest.mark.parametrize("N,K", [(7, 0), (7, 3), (6, 1), (5, 6)])
+def test_window_objective_is_the_mean_of_the_last_K_steps(lattice, dims, N, K):
+    # J = sum_n c_n F(f^n) with c_n = 1/K on n = N-K+1 .. N (K > 0), or the
+    # final step alone (K = 0), against the closed-form F(f^n) of the ghost
+    # mode: a window of K+1 terms, a weight 1/(K+1) or a shifted window
+    # fails it.  Both weight constructions of the oracle are checked (the
+    # problem's horizon and an explicit one).
+    tau = 0.7
+    P, o, F, closed = _ghost_mode(lattice, dims, tau, eps=0.03)
+    for n in range(3):                     # the closed form itself, step by step
+        assert abs(float(o.F_obj(F)) - closed(n)) <= 1e-12 * closed(0)
+        with torch.no_grad():
+            F = o.step(F)
+    want = closed(N) if K == 0 else sum(closed(n) for n in range(N - K + 1, N + 1)) / K
+    _, o, F0, _ = _ghost_mode(lattice, dims, tau, eps=0.03)
+    o.P = P.replace(nsteps=N, obj_window=K)
+    o.model.P = o.P
+    J_model, _ = o.primal(F0=F0, keep=False)              # weights of the problem (Model.weights)
+    J_explicit, _ = o.primal(nsteps=N, F0=F0, keep=False)  # weights of an explicit horizon
+    assert abs(J_model - want) <= 1e-12 * want
+    assert abs(J_explicit - want) <= 1e-12 * want
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_outlet_scalar_reconstruction_worked_example(lattice):
+    # One outlet node, fluid at equilibrium with u = (0.05, 0, 0) so that
+    # the Zou-He outlet (rho_out = 1) returns v = u.  The scalar populations
+    # that stream in from the interior (e_x >= 0) are set by hand to values
+    # summing to S = 0.45; the ones with e_x < 0, which would stream in from
+    # outside the box, hold garbage (7.0 each).  The outlet condition puts
+    # the unknowns at equilibrium with the node's own value T*, w_i T*
+    # (1 + e_i.v / cs2), and T* must be the zeroth moment of the
+    # reconstructed populations: T* = S + T* sum_unknown w_i (1 - 0.05 /
+    # cs2).  D3Q7 (cs2 = 1/4, one unknown of weight 1/8):
+    # T* = 0.45 / (1 - 0.8 / 8) = 0.5 exactly.  D2Q9 scalar (cs2 = 1/3,
+    # unknown weights 1/9, 1/36, 1/36): T* = 0.45 / (1 - 0.85 / 6).  A
+    # reconstruction that takes T* = sum g (here 0.45 + garbage) fails.
+    is3d = lattice == "D3Q19"
+    P = inputs.Problem(lattice=lattice, dims=(3, 1, 1), collision="BGK", tau=0.8, walls="",
+                       channel="inlet_outlet", u_in=0.05, rho_out=1.0, nscalars=1,
+                       alpha_fluid=0.1, alpha_solid=0.1, objective="heatflux")
+    o = Oracle(P, np.zeros((1, 1, 3), np.float32))
+    m = o.model
+    ux = 0.05
+    E = m.E.numpy()
+    w = m.w.numpy()
+    eu = E[:, 0] * ux
+    f = w * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * ux ** 2)
+    Es = m.sl.E
+    known = np.nonzero(Es[:, 0] >= 0)[0]
+    unk = np.nonzero(Es[:, 0] < 0)[0]
+    g = np.full(m.Qs, 7.0)
+    vals = [0.02, 0.05, 0.08, 0.11, 0.06, 0.09, 0.04, 0.0, 0.0][:len(known)]
+    vals[-1] += 0.45 - sum(vals)
+    g[known] = vals
+    F = torch.tensor(np.concatenate([f, g]), dtype=torch.float64)[:, None]
+    flags = torch.tensor([OUTLET])
+    mac = m.macroscopic(F, torch.zeros(1, dtype=torch.float64), flags)
+    v = mac["v"][:, 0].numpy()
+    assert abs(v[0] - ux) <= 1e-15 and abs(v[1]) <= 1e-15 and abs(v[2]) <= 1e-15
+    T_star = 0.5 if is3d else 0.45 / (1 - 0.85 / 6)
+    assert abs(float(mac["T"][0][0]) - T_star) <= 1e-14
+    gr = mac["gr"][0][:, 0].numpy()
+    np.testing.assert_allclose(gr[known], g[known], rtol=0, atol=0)
+    cs2 = 0.25 if is3d else 1.0 / 3.0
+    want_unk = m.sl.w[unk] * T_star * (1 - ux / cs2)
+    np.testing.assert_allclose(gr[unk], want_unk, rtol=0, atol=1e-15)
+    # the heat flux of this node is v_x T*
+    assert abs(float(o.model.objective(F, torch.zeros(1, dtype=torch.float64), flags,
+                                       torch.zeros(1, dtype=torch.long))) - ux * T_star) <= 1e-15
