@@ -349,10 +349,11 @@ lbm_status lbm_get_theta(lbm_handle h, float* dst);
 
 /* Objective F(f) of one pre-collision state, evaluated without allocating
  * any device memory.  The paper has no counterpart: this entry point exists
- * for callers that cannot allocate at the point of the call - code running
- * while a stream is captured into a CUDA graph (cudaMalloc is not
- * capturable and synchronises the device), processes whose device memory is
- * fully handed out in advance, and host frameworks that own the allocator.
+ * for callers that cannot allocate at the point of the call - a serving
+ * process whose device memory is fully reserved in advance for resident
+ * states, plugins inside a host framework that owns the device allocator
+ * and forbids allocations behind its back, and code that must not pay the
+ * device-wide synchronisation cudaFree implies while other streams run.
  *   p      : problem description (lattice, collision, objective, ...); the
  *            time weights are ignored, F is the objective of this one state.
  *   f      : device, M*N floats, full pre-collision populations (the layout
@@ -360,12 +361,14 @@ lbm_status lbm_get_theta(lbm_handle h, float* dst);
  *   theta  : device, N floats.   flags: device, N node types.
  *   stream : cudaStream_t the two kernels run on.
  *   F_host : host pointer receiving F; the call synchronises the stream.
- * Scratch lives in a fixed static device array of about 1.5 MiB that every
- * GPU loading the library keeps until exit; lattices above 8,388,608 nodes
- * are rejected with LBM_ERR_ARG.  The first call on a device, with that
- * device current, resolves the array's device address; make it before any
- * stream capture.  All calls share the array, so calls that overlap on the
- * GPU race and must be serialised by the caller.  Errors: LBM_ERR_ARG,
+ * The C ABI takes no buffer sizes: f, theta and flags must hold the M*N,
+ * N and N elements that p implies.  Scratch lives in a fixed static device
+ * array of about 1.5 MiB that every GPU loading the library keeps until
+ * exit; lattices above 8,388,608 nodes are rejected with LBM_ERR_ARG.  The
+ * first call on a device, with that device current, resolves the array's
+ * device address and loads the entry point's kernels; later calls on that
+ * device only launch.  All calls share the array, so calls that overlap on
+ * the GPU race and must be serialised by the caller.  Errors: LBM_ERR_ARG,
  * LBM_ERR_CUDA; the message is returned by lbm_noalloc_last_error(). */
 lbm_status lbm_state_objective_noalloc(const lbm_params* p, const float* f,
                                        const float* theta, const uint8_t* flags,

@@ -426,11 +426,27 @@ class Solver:
 def state_objective_noalloc(P: Problem, f, theta, flags, stream=None) -> float:
     """F(f) of one pre-collision state through the allocation-free entry point.
 
-    ``f`` (M x N float32), ``theta`` (N float32) and ``flags`` (N uint8) must
-    be device tensors.  The library allocates no device memory for this call
-    (its scratch is a fixed static device array); concurrent calls on one
-    device must not overlap.
+    For callers that cannot allocate device memory when they need an
+    objective value (a process whose device memory is reserved in advance, a
+    host framework that owns the allocator).  ``f`` (M x N float32),
+    ``theta`` (N float32) and ``flags`` (N uint8) must be contiguous CUDA
+    tensors of exactly those sizes: the C entry point takes no buffer sizes,
+    so they are checked here before the call.  The library allocates no
+    device memory for this call (its scratch is a fixed static device
+    array); calls on one device must not overlap.
     """
+    import torch
+    Q = 9 if P.lattice == "D2Q9" else 19
+    Qs = 9 if P.lattice == "D2Q9" else 7
+    M = Q + int(P.nscalars) * Qs
+    N = P.n_nodes
+    for name, t, dtype, n in (("f", f, torch.float32, M * N), ("theta", theta, torch.float32, N),
+                              ("flags", flags, torch.uint8, N)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dtype or t.numel() != n or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor of {n} elements "
+                             f"(got {t.dtype}, {t.numel()} elements)")
     L = lib()
     p = make_params(P)
     F = C.c_double()

@@ -2,14 +2,16 @@
 // state, evaluated without allocating device memory.
 //
 // Why it exists.  Some callers cannot call cudaMalloc at the moment they
-// need an objective value: code running while a stream is being captured
-// into a CUDA graph (allocation is not capturable and the implicit device
-// synchronisation of cudaMalloc/cudaFree breaks the capture), host code that
-// runs under a fixed device-memory budget that is already fully handed out
-// (for example a serving process whose HBM is reserved for resident
-// states), and plugins inside a host framework that owns the device
-// allocator and forbids side allocations.  This entry point therefore uses
-// a fixed scratch array in the library's own static device memory.
+// need an objective value: a serving process whose device memory is fully
+// reserved in advance for resident states (an extra allocation would fail,
+// or would take memory promised to a request), plugins inside a host
+// framework that owns the device allocator and forbids allocations behind
+// its back (they would fragment the framework's pool and make its own later
+// allocations fail), and code that must not pay the device-wide
+// synchronisation that cudaFree implies while other streams run.  This
+// entry point therefore uses a fixed scratch array in the library's own
+// static device memory; the caller passes the inputs, and the result comes
+// back in a host double (the call synchronises the given stream).
 //
 // Scratch.  g_noalloc_scratch below is a file-scope __device__ array of
 // kNoAllocMaxBlocks * kSlots doubles plus one result row (about 1.5 MiB).
@@ -24,8 +26,10 @@
 // Host code may not hand the symbol itself to a kernel: in host code
 // g_noalloc_scratch names a host-side stand-in, not a device address.  The
 // first call on each device (with that device current) looks the device
-// address up with cudaGetSymbolAddress and caches it; make that first call
-// before any stream capture begins.
+// address up with cudaGetSymbolAddress, checks the result, caches it, and
+// loads every kernel this file holds (so that later calls with another
+// lattice or collision load nothing); it is the only call that does this
+// set-up.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -150,6 +154,26 @@ cudaError_t dispatch(const lbm_params& p, const albm::KParams& P, const float* f
   }
 }
 
+// With lazy module loading a kernel is loaded on its first launch, which
+// may allocate device memory; querying the attributes of every kernel of
+// this file loads them all up front, on the current device.
+cudaError_t load_all_kernels() {
+  using namespace albm;
+  cudaFuncAttributes a;
+  const void* k[] = {
+      (const void*)noalloc_pass1<D2Q9, 0, false>,  (const void*)noalloc_pass1<D2Q9, 0, true>,
+      (const void*)noalloc_pass1<D2Q9, 1, false>,  (const void*)noalloc_pass1<D2Q9, 1, true>,
+      (const void*)noalloc_pass1<D3Q19, 0, false>, (const void*)noalloc_pass1<D3Q19, 0, true>,
+      (const void*)noalloc_pass1<D3Q19, 1, false>, (const void*)noalloc_pass1<D3Q19, 1, true>,
+      (const void*)noalloc_pass1<D3Q19, 2, false>, (const void*)noalloc_pass1<D3Q19, 2, true>,
+      (const void*)noalloc_pass2};
+  for (const void* f : k) {
+    cudaError_t e = cudaFuncGetAttributes(&a, f);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 lbm_status fail(lbm_status code, const std::string& msg) {
   g_err = msg;
   return code;
@@ -172,8 +196,13 @@ extern "C" lbm_status lbm_state_objective_noalloc(const lbm_params* pp, const fl
     return fail(LBM_ERR_ARG, "nscalars out of range");
   if (!(p.tau > 0.5) || p.objective < LBM_OBJ_DISSIPATION || p.objective > LBM_OBJ_HEATFLUX)
     return fail(LBM_ERR_ARG, "tau must exceed 1/2 and an objective must be set");
-  if (p.objective >= LBM_OBJ_VARIANCE && p.nscalars < 1)
-    return fail(LBM_ERR_ARG, "outlet objectives need a scalar lattice");
+  if (p.objective >= LBM_OBJ_VARIANCE && (p.nscalars < 1 || !p.inlet_outlet))
+    return fail(LBM_ERR_ARG, "outlet objectives need a scalar lattice and inlet_outlet");
+  if (p.inlet_outlet && (p.nx < 3 || !(p.u_in < 1.0) || !(p.rho_out > 0.0)))
+    return fail(LBM_ERR_ARG, "inlet_outlet needs nx >= 3, u_in < 1 and rho_out > 0");
+  if (p.porosity < 0 || p.porosity > 2) return fail(LBM_ERR_ARG, "unknown porosity law");
+  if (p.scalar_inlet < 0 || p.scalar_inlet > 2)
+    return fail(LBM_ERR_ARG, "unknown scalar inlet profile");
   const long long N = (long long)p.nx * p.ny * p.nz;
   if (N > kNoAllocMaxNodes) {
     char b[160];
@@ -193,6 +222,9 @@ extern "C" lbm_status lbm_state_objective_noalloc(const lbm_params* pp, const fl
       e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);   // device address, this device
       if (e != cudaSuccess)
         return fail(LBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      e = load_all_kernels();
+      if (e != cudaSuccess)
+        return fail(LBM_ERR_CUDA, std::string("loading the kernels: ") + cudaGetErrorString(e));
       g_dev_ptr[dev] = (double*)ptr;
     }
     scratch = g_dev_ptr[dev];
