@@ -115,6 +115,11 @@ typedef struct {
                            copied to shared memory by TMA bulk copies (2)
                            or by per-thread cp.async (3); nx a multiple of
                            128                                              */
+  int adjoint_mode;     /* 0: unsteady adjoint over the trajectory (exact
+                           gradient of J over the horizon); 1: the paper's
+                           fixed-point ALBS at the held state f-hat = f^N
+                           (Sec. 2.2, Eqs. adjoint:iteration/adjoint:operator
+                           at the stationary state), needs obj_window 0      */
 } lbm_params;
 
 /* Create a solver.  Defines the lattice, node types, collision (Sec. 3,
@@ -156,12 +161,24 @@ int lbm_time(lbm_handle h);
  * Synchronises the stream.  J_host: host pointer to one double. */
 lbm_status lbm_objective(lbm_handle h, double* J_host);
 
-/* Run k adjoint steps backward in time (Eq. adjoint:iteration, unsteady
- * form).  The first call starts at the current primal time n = T with
+/* Run k adjoint steps.
+ * adjoint_mode 0 (unsteady; Eq. adjoint:iteration applied backward in
+ * time): the first call starts at the current primal time n = T with
  * lambda^T = c_T dF/df(f^T) and zeroes the gradient; each step computes
  * lambda^{n} from lambda^{n+1} and f^n (restored from checkpoints by
  * recomputation when it was not kept) and adds its theta terms to the FP64
- * gradient.  Errors: LBM_ERR_STATE when k exceeds the remaining steps. */
+ * gradient.  Errors: LBM_ERR_STATE when k exceeds the remaining steps.
+ * adjoint_mode 1 (the paper's ALBS, Sec. 2.2): k iterations of
+ *   v^k = (d(SW)/df(f-hat))^T v^{k-1} + dF/df(f-hat)
+ * at the held state f-hat = the current primal state (f^N after a full
+ * primal run), starting from v^0 = 0 (or the lbm_adjoint_seed vector) on
+ * the first call.  Each iteration overwrites the gradient with Eq.
+ * adjoint:derivative evaluated with the iterate it consumes,
+ *   dJ/dtheta = (d(SW)/dtheta(f-hat))^T v^{k-1} + dF/dtheta(f-hat),
+ * which converges to the gradient of the stationary objective F(f-hat)
+ * when f-hat is a fixed point of the primal.  Any k >= 0 is allowed;
+ * lbm_get_adjoint returns v^k.  The batched adjoint does not take this
+ * mode (LBM_ERR_ARG). */
 lbm_status lbm_adjoint_step(lbm_handle h, int k);
 
 /* Start the adjoint at the current primal time T with lambda^T = lam (M*N
@@ -173,7 +190,9 @@ lbm_status lbm_adjoint_seed(lbm_handle h, const float* lam);
 /* Current adjoint time n (lambda^n is held); -1 before the adjoint starts. */
 int lbm_adjoint_time(lbm_handle h);
 
-/* Full sensitivity solve: reset, nsteps primal steps, nsteps adjoint steps.
+/* Full sensitivity solve: reset, nsteps primal steps, nsteps adjoint steps
+ * (unsteady), or nsteps primal steps followed by the same number of ALBS
+ * iterations at f^N (adjoint_mode 1, the schedule of Sec. 3.3).
  * Equivalent to lbm_reset + lbm_primal_step(N) + lbm_adjoint_step(N). */
 lbm_status lbm_run(lbm_handle h);
 
@@ -206,6 +225,14 @@ lbm_status lbm_get_flags(lbm_handle h, uint8_t* dst);
 /* Count non-finite values in the current state (0 = healthy); synchronises.
  * Returns LBM_ERR_NONFINITE when the count is positive. */
 lbm_status lbm_check_finite(lbm_handle h, long long* count_host);
+
+/* Move the handle to another CUDA stream (NULL = legacy default).  Work
+ * already queued for the handle on its old stream is ordered before any
+ * later work on the new one (an event recorded on the old stream, waited
+ * for on the new one); nothing is synchronised on the host.  Lets a
+ * scheduler give each group of batched handles its own stream.  Errors:
+ * LBM_ERR_ARG, LBM_ERR_CUDA. */
+lbm_status lbm_set_stream(lbm_handle h, void* stream);
 
 /* Sizes: M densities per node and N nodes. */
 lbm_status lbm_sizes(lbm_handle h, int* M, long long* N);
@@ -249,6 +276,15 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k);
  * handle whose adjoint has not started starts at its current primal time.
  * Same requirements and errors as lbm_batch_primal_step. */
 lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k);
+
+/* As lbm_batch_primal_step / lbm_batch_adjoint_step with a step count per
+ * handle: handle i advances by up to ks[i] >= 0 steps (host array of n
+ * ints); every step's launch covers the handles that still have steps left
+ * in this call.  A scheduler that gives requests of different sizes
+ * different step counts (equal work per request) makes one call per group
+ * instead of one per step.  Same requirements and errors. */
+lbm_status lbm_batch_primal_steps(const lbm_handle* hs, int n, const int* ks);
+lbm_status lbm_batch_adjoint_steps(const lbm_handle* hs, int n, const int* ks);
 
 /* ---- one-shot optimisation (Sec. 3.3) -------------------------------------
  * The design theta is optimised together with the flow.  One iteration:

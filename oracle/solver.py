@@ -277,12 +277,18 @@ class Oracle:
         return [self.steady_objective(nsteps, self.threshold(theta, e, design)) for e in etas]
 
     # --- MMA design iterations (Sec. 3.3, oracle.mma) ------------------------
-    def mma(self, iters, maximize=True, design=None, prm=None):
-        """MMA as Sec. 3.3 runs it: per design iteration a full solve (here
-        the N-step primal and the unsteady adjoint, exact dJ/dtheta), then one
+    def mma(self, iters, maximize=True, design=None, prm=None, adjoint="unsteady"):
+        """MMA as Sec. 3.3 runs it: per design iteration a full solve, then one
         MMA update of theta on the design nodes (``oracle.mma.update``; a
         maximised J is minimised as -J).  Returns (theta, [J per iteration],
-        MMA state)."""
+        MMA state).
+
+        adjoint="unsteady": the N-step primal and the unsteady adjoint (exact
+        dJ/dtheta of the horizon's J).  adjoint="frozen": the N-step primal,
+        then N iterations of the ALBS at f^N (Sec. 3.3 iterates the adjoint
+        as many times as the primal); the gradient of Eq. adjoint:derivative
+        is taken with the iterate the N-th iteration consumes, v^{N-1}, i.e.
+        ``frozen_adjoint(f^N, N - 1)``."""
         from . import mma as M
         prm = prm or M.MMAParams()
         th = self.theta.numpy().astype(np.float64).copy()
@@ -293,7 +299,11 @@ class Oracle:
         try:
             for _ in range(int(iters)):
                 self.theta = torch.as_tensor(th)
-                J, g, _ = self.gradient()
+                if adjoint == "frozen":
+                    J, traj = self.primal(keep=False)
+                    g, _ = self.frozen_adjoint(traj[-1], int(self.P.nsteps) - 1)
+                else:
+                    J, g, _ = self.gradient()
                 hist.append(J)
                 g = g.reshape(-1).numpy()
                 th = M.update(state, th, -g if maximize else g, mask, prm)

@@ -27,6 +27,7 @@ OBJECTIVE = {"none": 0, "dissipation": 1, "variance": 2, "heatflux_dp": 3, "mixf
              "heatflux": 5}
 SCALAR_INLET = {"zero": 0, "halves": 1, "signed": 2}
 KERNEL = {"auto": 0, "plain": 1, "tiles": 2, "async": 3}
+ADJOINT_MODE = {"unsteady": 0, "frozen": 1}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
           4: "LBM_ERR_NONFINITE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 
@@ -41,7 +42,8 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_theta", "lbm_
            "lbm_oneshot_step", "lbm_oneshot_eval", "lbm_threshold_scan",
            "lbm_threshold_apply", "lbm_get_theta", "lbm_mma_reset", "lbm_mma_update",
            "lbm_mma_update_with", "lbm_state_objective_noalloc",
-           "lbm_noalloc_last_error"]
+           "lbm_noalloc_last_error", "lbm_set_stream", "lbm_batch_primal_steps",
+           "lbm_batch_adjoint_steps"]
 
 
 class LbmParams(C.Structure):
@@ -54,7 +56,7 @@ class LbmParams(C.Structure):
         ("hot", C.c_int * 4), ("T_hot", C.c_double), ("porosity", C.c_int),
         ("porosity_q", C.c_double), ("objective", C.c_int), ("obj_window", C.c_int),
         ("nsteps", C.c_int), ("precision", C.c_int), ("ckpt_every", C.c_int),
-        ("mem_budget", C.c_double), ("kernel", C.c_int),
+        ("mem_budget", C.c_double), ("kernel", C.c_int), ("adjoint_mode", C.c_int),
     ]
 
 
@@ -103,6 +105,8 @@ def lib():
         L.lbm_recompute_steps.restype = C.c_longlong
         L.lbm_batch_primal_step.argtypes = [C.POINTER(vp), i, i]
         L.lbm_batch_adjoint_step.argtypes = [C.POINTER(vp), i, i]
+        L.lbm_batch_primal_steps.argtypes = [C.POINTER(vp), i, C.POINTER(i)]
+        L.lbm_batch_adjoint_steps.argtypes = [C.POINTER(vp), i, C.POINTER(i)]
         L.lbm_set_design.argtypes = [vp, vp]
         L.lbm_oneshot_reset.argtypes = [vp]
         L.lbm_oneshot_step.argtypes = [vp, i, d, d, i]
@@ -113,6 +117,7 @@ def lib():
         L.lbm_mma_reset.argtypes = [vp]
         L.lbm_mma_update.argtypes = [vp, i, d]
         L.lbm_mma_update_with.argtypes = [vp, vp, i, d]
+        L.lbm_set_stream.argtypes = [vp, vp]
         L.lbm_state_objective_noalloc.argtypes = [C.POINTER(LbmParams), vp, vp, vp, vp,
                                                   C.POINTER(d)]
         L.lbm_noalloc_last_error.argtypes = []
@@ -151,6 +156,7 @@ def make_params(P: Problem, mem_budget: float = 0.0) -> LbmParams:
     p.ckpt_every = int(P.ckpt_every)
     p.mem_budget = float(mem_budget)
     p.kernel = KERNEL[P.kernel]
+    p.adjoint_mode = ADJOINT_MODE[P.adjoint_mode]
     return p
 
 
@@ -324,6 +330,14 @@ class Solver:
         self._sync_out()
         return out
 
+    def set_stream(self, stream):
+        """Move the handle to ``stream`` (a torch.cuda.Stream); its queued work
+        is ordered before later work on the new stream."""
+        if stream is self.stream:
+            return
+        self._check(self._L.lbm_set_stream(self._h, _stream_ptr(stream)))
+        self.stream = stream
+
     def flags(self) -> np.ndarray:
         out = np.empty(self.N, dtype=np.uint8)
         self._check(self._L.lbm_get_flags(self._h, _ptr(out)))
@@ -464,17 +478,32 @@ def _handles(solvers):
     return arr
 
 
-def batch_primal_step(solvers, k: int = 1):
-    """Advance every solver by up to k primal steps in batched launches."""
+def _steps(k, n):
+    """A step count for every solver: one int for all, or a list of n."""
+    if isinstance(k, (list, tuple)):
+        if len(k) != n:
+            raise ValueError("one step count per solver is required")
+        return (C.c_int * n)(*[int(v) for v in k])
+    return None
+
+
+def batch_primal_step(solvers, k=1):
+    """Advance every solver by up to k primal steps in batched launches (k an
+    int, or a list with one count per solver)."""
     L = lib()
-    code = L.lbm_batch_primal_step(_handles(solvers), len(solvers), int(k))
+    ks = _steps(k, len(solvers))
+    code = (L.lbm_batch_primal_steps(_handles(solvers), len(solvers), ks) if ks is not None
+            else L.lbm_batch_primal_step(_handles(solvers), len(solvers), int(k)))
     if code != 0:
         raise AlbmError(code, L.lbm_last_error(solvers[0]._h).decode())
 
 
-def batch_adjoint_step(solvers, k: int = 1):
-    """Run up to k adjoint steps on every solver in batched launches."""
+def batch_adjoint_step(solvers, k=1):
+    """Run up to k adjoint steps on every solver in batched launches (k an int,
+    or a list with one count per solver)."""
     L = lib()
-    code = L.lbm_batch_adjoint_step(_handles(solvers), len(solvers), int(k))
+    ks = _steps(k, len(solvers))
+    code = (L.lbm_batch_adjoint_steps(_handles(solvers), len(solvers), ks) if ks is not None
+            else L.lbm_batch_adjoint_step(_handles(solvers), len(solvers), int(k)))
     if code != 0:
         raise AlbmError(code, L.lbm_last_error(solvers[0]._h).decode())

@@ -46,13 +46,19 @@ def _deps() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
+def _env_flags():
+    """Extra nvcc flags from ALBM_NVCC_FLAGS (e.g. -D switches of the kernels)."""
+    import shlex
+    return shlex.split(os.environ.get("ALBM_NVCC_FLAGS", ""))
+
+
 def _compile(unit: str, force: bool, verbose: bool, extra) -> str:
     src = os.path.join(CSRC, unit)
     obj = os.path.join(OBJ_DIR, unit.replace(".cu", ".o"))
     if (not force and os.path.exists(obj)
             and os.path.getmtime(obj) >= max(os.path.getmtime(src), _deps())):
         return obj
-    cmd = [nvcc()] + NVFLAGS + list(extra) + ["-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc()] + NVFLAGS + _env_flags() + list(extra) + ["-c", src, "-o", obj + ".tmp"]
     if verbose:
         print(" ".join(cmd), flush=True)
     res = subprocess.run(cmd, capture_output=True, text=True)

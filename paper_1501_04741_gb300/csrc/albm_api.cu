@@ -54,6 +54,12 @@ struct lbm_ctx {
   float* lam[2] = {nullptr, nullptr};
   int lam_cur = 0;
   size_t state_bytes = 0;
+  size_t state_stride = 0;          // state_bytes rounded up to 256
+  int slab_states = 1;              // states per allocation (small states share slabs)
+  std::vector<void*> slabs;         // allocations holding several states
+  char* slab_next = nullptr;
+  int slab_left = 0;
+  std::vector<char> buf_in_slab;
   std::vector<void*> bufs;
   std::vector<int> buf_time;        // time held by each buffer, -1 = free
   int max_bufs = 3;
@@ -82,6 +88,9 @@ struct lbm_ctx {
   // MMA history: x^{k-1}, x^{k-2}, last asymptotes (FP32, N each)
   float* mma_hist = nullptr;
   int mma_k = -1;                   // -1: lbm_mma_reset not called
+  // fixed-point ALBS at the held state (adjoint_mode 1): iterations done
+  int frozen_k = 0;
+  bool frozen_seeded = false;       // v^0 given by lbm_adjoint_seed (else 0)
   std::string err;
 };
 
@@ -169,8 +178,23 @@ static lbm_status acquire(lbm_ctx* h, int* out) {
     FAIL(h, LBM_ERR_OOM, "state pool exhausted (%d buffers of %zu bytes)", h->max_bufs,
          h->state_bytes);
   void* p = nullptr;
-  CK(h, cudaMalloc(&p, h->state_bytes));
+  if (h->slab_states > 1) {
+    if (h->slab_left == 0) {
+      const int n = std::min(h->slab_states, h->max_bufs - (int)h->bufs.size());
+      void* slab = nullptr;
+      CK(h, cudaMalloc(&slab, (size_t)n * h->state_stride));
+      h->slabs.push_back(slab);
+      h->slab_next = (char*)slab;
+      h->slab_left = n;
+    }
+    p = h->slab_next;
+    h->slab_next += h->state_stride;
+    h->slab_left--;
+  } else {
+    CK(h, cudaMalloc(&p, h->state_bytes));
+  }
   h->bufs.push_back(p);
+  h->buf_in_slab.push_back(h->slab_states > 1 ? 1 : 0);
   h->buf_time.push_back(-1);
   *out = (int)h->bufs.size() - 1;
   return LBM_OK;
@@ -424,11 +448,17 @@ static lbm_status ensure_state(lbm_ctx* h, int n) {
   }
   int cur = cb;
   int scratch[2] = {-1, -1};
+  // on failure the scratch buffers go back to the pool (kept states stay valid)
+  auto release = [&](lbm_status s) {
+    for (int j = 0; j < 2; ++j)
+      if (scratch[j] >= 0 && h->buf_time[scratch[j]] == -2) h->buf_time[scratch[j]] = -1;
+    return s;
+  };
   for (int k = 1; k <= L; ++k) {
     int dst;
     if (keep[k]) {
       lbm_status s = acquire(h, &dst);
-      if (s) return s;
+      if (s) return release(s);
     } else {
       // a scratch buffer that is not the source
       int pick = -1;
@@ -436,14 +466,14 @@ static lbm_status ensure_state(lbm_ctx* h, int n) {
         if (scratch[j] >= 0 && scratch[j] != cur) pick = scratch[j];
       if (pick < 0) {
         lbm_status s = acquire(h, &pick);
-        if (s) return s;
+        if (s) return release(s);
         h->buf_time[pick] = -2;  // reserved as scratch
         if (scratch[0] < 0) scratch[0] = pick; else scratch[1] = pick;
       }
       dst = pick;
     }
     lbm_status s = launch_primal(h, cur, dst, c + k - 1, false, K_RECOMPUTE);
-    if (s) return s;
+    if (s) return release(s);
     h->recompute_steps++;
     if (keep[k]) h->buf_time[dst] = c + k;
     else h->buf_time[dst] = -2;
@@ -482,7 +512,14 @@ static lbm_status do_reset(lbm_ctx* h) {
   int b;
   lbm_status s = acquire(h, &b);
   if (s) return s;
-  CK(h, cudaMemsetAsync(h->bufs[b], 0, h->state_bytes, h->stream));  // f^0 = rest state
+  if (h->ks.storage_bytes == 4) {
+    CK(h, cudaMemsetAsync(h->bufs[b], 0, h->state_bytes, h->stream));  // f^0 = rest state
+  } else {
+    StepArgs a = blank_args(h);   // rest state relative to the reference offsets
+    a.Bout = h->bufs[b];
+    CK(h, h->ks.rest(h->kp, a, h->stream));
+    h->launches_other++;
+  }
   h->buf_time[b] = 0;
   h->t = 0;
   h->t_adj = -1;
@@ -512,6 +549,8 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   lbm_status st = LBM_OK;
   if (p.lattice != LBM_D2Q9 && p.lattice != LBM_D3Q19) st = bad("lattice must be D2Q9 or D3Q19");
   else if (p.nx < 1 || p.ny < 1 || p.nz < 1) st = bad("lattice sizes must be positive");
+  else if ((long long)p.nx * p.ny * p.nz >= (1LL << 31) - 1024)
+    st = bad("lattices of 2^31 nodes or more are not supported (32-bit node indices)");
   else if (p.lattice == LBM_D2Q9 && p.nz != 1) st = bad("D2Q9 needs nz == 1");
   else if (p.lattice == LBM_D2Q9 && p.force[2] != 0.0) st = bad("D2Q9 needs force[2] == 0");
   else if (p.collision != LBM_BGK && p.collision != LBM_MRT) st = bad("collision must be BGK or MRT");
@@ -529,6 +568,9 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   else if (p.porosity == LBM_POR_POWER && p.porosity_q < 1.0) st = bad("power porosity needs q >= 1");
   else if (p.inlet_outlet && (p.nx < 3 || !(p.u_in < 1.0) || !(p.rho_out > 0.0)))
     st = bad("inlet_outlet needs nx >= 3, u_in < 1 and rho_out > 0");
+  else if (p.adjoint_mode < 0 || p.adjoint_mode > 1) st = bad("adjoint_mode must be 0 or 1");
+  else if (p.adjoint_mode == 1 && p.obj_window != 0)
+    st = bad("the fixed-point adjoint (adjoint_mode 1) needs obj_window 0: J = F(f^N)");
   else if (!theta) st = bad("theta must not be NULL");
   if (st) {
     *out = h;  // so that lbm_last_error can report; caller destroys
@@ -554,6 +596,9 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   k.nz = p.nz;
   k.nscal = p.nscalars;
   k.N = h->N;
+  k.fd_nx = albm::make_fastdiv((unsigned)p.nx);
+  k.fd_ny = albm::make_fastdiv((unsigned)p.ny);
+  k.fd_hx = albm::make_fastdiv((unsigned)std::max(p.nx / 2, 1));
   const double omega = 1.0 / p.tau;
   k.omega = (float)omega;
   k.one_m_omega = (float)(1.0 - omega);
@@ -577,7 +622,19 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
     if (p.lattice == LBM_D3Q19) albm::fill_mrt<albm::D3Q19>(omega, p.s_other, k);
     else albm::fill_mrt<albm::D2Q9>(omega, p.s_other, k);
   }
+  if (p.precision != LBM_FP32) {
+    // 16-bit storage holds deviations from the equilibrium at the inlet
+    // velocity (rest for periodic channels)
+    const double u_ref[3] = {p.inlet_outlet ? p.u_in : 0.0, 0.0, 0.0};
+    if (p.lattice == LBM_D3Q19) albm::fill_dev_off<albm::D3Q19>(u_ref, k);
+    else albm::fill_dev_off<albm::D2Q9>(u_ref, k);
+  }
   h->state_bytes = (size_t)h->M * (size_t)h->N * (size_t)h->ks.storage_bytes;
+  h->state_stride = (h->state_bytes + 255) / 256 * 256;
+  // states below 2 MiB (the granularity of cudaMalloc's mappings) are
+  // carved out of 32 MiB slabs, so that a pool of many small states costs
+  // its bytes and not a page per state
+  h->slab_states = h->state_stride < (2u << 20) ? (int)((32u << 20) / h->state_stride) : 1;
   // time weights c_n of J = sum_n c_n F(f^n)
   h->c.assign((size_t)p.nsteps + 1, 0.0);
   if (p.objective != LBM_OBJ_NONE) {
@@ -659,7 +716,7 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
     CKC(cudaMemGetInfo(&fr, &tot));
     budget = 0.90 * (double)fr;
   }
-  h->max_bufs = (int)std::max(3.0, std::floor(budget / (double)h->state_bytes));
+  h->max_bufs = (int)std::max(3.0, std::floor(budget / (double)h->state_stride));
   // level-1 checkpoint stride: given, or every state if all fit, else
   // spread over half of the pool
   if (p.ckpt_every > 0) h->ckpt = p.ckpt_every;
@@ -679,7 +736,9 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
 void lbm_destroy(lbm_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (void* b : h->bufs) cudaFree(b);
+  for (size_t i = 0; i < h->bufs.size(); ++i)
+    if (!h->buf_in_slab[i]) cudaFree(h->bufs[i]);
+  for (void* b : h->slabs) cudaFree(b);
   cudaFree(h->flags);
   cudaFree(h->theta);
   cudaFree(h->grad);
@@ -776,6 +835,49 @@ lbm_status lbm_objective(lbm_handle h, double* J) {
   return LBM_OK;
 }
 
+// ---- fixed-point ALBS at the held state (Sec. 2.2) -------------------------
+// v^k = (d(SW)/df(f-hat))^T v^{k-1} + dF/df(f-hat) with f-hat the current
+// primal state, v^0 = 0 (or the seed); each iteration also writes the
+// gradient estimate of Eq. adjoint:derivative from the iterate it consumes.
+static lbm_status state_objective(lbm_ctx* h, int b);
+
+static lbm_status frozen_start(lbm_ctx* h) {
+  const int b = find_buf(h, h->t);
+  if (b < 0) FAIL(h, LBM_ERR_STATE, "the current primal state is not held");
+  CK(h, cudaMemsetAsync(h->grad, 0, sizeof(double) * (size_t)h->N, h->stream));
+  h->lam_cur = 0;
+  h->t_adj = h->t;
+  h->frozen_k = 0;
+  h->frozen_seeded = false;
+  if (h->p.objective == LBM_OBJ_VARIANCE) {
+    // the variance source needs the outlet mean of f-hat
+    if (!h->os_stats) CK(h, cudaMalloc(&h->os_stats, 2 * sizeof(double)));
+    lbm_status s = state_objective(h, b);
+    if (s) return s;
+  }
+  return LBM_OK;
+}
+
+static lbm_status frozen_iteration(lbm_ctx* h) {
+  StepArgs a = blank_args(h);
+  a.Bin = h->bufs[find_buf(h, h->t_adj)];
+  a.lam_in = h->lam[h->lam_cur];
+  a.lam_out = h->lam[1 - h->lam_cur];
+  a.grad = h->grad;
+  a.ws = 1.0f;
+  a.stat_n = h->p.objective == LBM_OBJ_VARIANCE ? h->os_stats : nullptr;
+  a.has_next = (h->frozen_k > 0 || h->frozen_seeded) ? 1 : 0;   // v^0 = 0 needs no gather
+  a.os.overwrite = 1;
+  int slot;
+  prof_begin(h, K_ADJOINT, &slot);
+  cudaError_t e = h->ks.adjoint(h->kp, a, h->stream);
+  prof_end(h, slot);
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "adjoint kernel launch: %s", cudaGetErrorString(e));
+  h->lam_cur = 1 - h->lam_cur;
+  h->frozen_k++;
+  return LBM_OK;
+}
+
 static lbm_status adjoint_start(lbm_handle h) {
   CK(h, cudaMemsetAsync(h->grad, 0, sizeof(double) * (size_t)h->N, h->stream));
   h->lam_cur = 0;
@@ -789,6 +891,19 @@ lbm_status lbm_adjoint_step(lbm_handle h, int k) {
   if (k < 0) FAIL(h, LBM_ERR_ARG, "negative step count");
   if (h->oneshot) FAIL(h, LBM_ERR_STATE, "a one-shot run is active; reset first");
   CK(h, cudaEventRecord(h->t2, h->stream));
+  if (h->p.adjoint_mode == 1) {
+    if (h->t_adj < 0) {
+      lbm_status s = frozen_start(h);
+      if (s) return s;
+    }
+    for (int i = 0; i < k; ++i) {
+      lbm_status s = frozen_iteration(h);
+      if (s) return s;
+    }
+    CK(h, cudaEventRecord(h->t3, h->stream));
+    h->adjoint_timed = true;
+    return LBM_OK;
+  }
   if (h->t_adj < 0) {
     lbm_status s = adjoint_start(h);
     if (s) return s;
@@ -813,6 +928,11 @@ lbm_status lbm_adjoint_step(lbm_handle h, int k) {
 lbm_status lbm_adjoint_seed(lbm_handle h, const float* lam) {
   if (!h || !lam) return LBM_ERR_ARG;
   if (find_buf(h, h->t) < 0) FAIL(h, LBM_ERR_STATE, "current state not held");
+  if (h->p.adjoint_mode == 1 && !h->oneshot) {
+    lbm_status s = frozen_start(h);
+    if (s) return s;
+    h->frozen_seeded = true;
+  }
   CK(h, cudaMemsetAsync(h->grad, 0, sizeof(double) * (size_t)h->N, h->stream));
   h->lam_cur = 0;
   h->t_adj = h->t;
@@ -898,26 +1018,47 @@ struct BatchMove {
   bool alone;
 };
 
-lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
+// Batched primal steps; handle i stops at time stop[i] (its horizon at most).
+static lbm_status batch_primal(const lbm_handle* hs, int n, const int* ks, int kall) {
   lbm_status st = batch_check(hs, n);
   if (st) return st;
-  for (int i = 0; i < n; ++i)
+  std::vector<int> stop((size_t)n);
+  int k = 0;
+  for (int i = 0; i < n; ++i) {
     if (hs[i]->t_adj >= 0) FAIL(hs[i], LBM_ERR_STATE, "the adjoint of this trajectory has started");
+    const int ki = ks ? ks[i] : kall;
+    if (ki < 0) FAIL(hs[0], LBM_ERR_ARG, "negative step count");
+    stop[(size_t)i] = (int)std::min<long long>((long long)hs[i]->t + ki, hs[i]->p.nsteps);
+    k = std::max(k, ki);
+  }
   static thread_local albm::BatchArgs args;
   for (int step = 0; step < k; ++step) {
     args.n = 0;
     long long blocks = 0;
     std::vector<BatchMove> moved;
+    // on failure: instances that ran their own launch keep their new state,
+    // the others give back the buffer reserved for the batched launch
+    auto unwind = [&](lbm_ctx* hf, lbm_status s) {
+      for (auto& m : moved) {
+        if (m.alone) {
+          m.h->buf_time[m.dst] = m.h->t + 1;
+          m.h->t += 1;
+        } else if (m.h->buf_time[m.dst] == -2) {
+          m.h->buf_time[m.dst] = -1;
+        }
+      }
+      return batch_fail(hs[0], hf, s);
+    };
     for (int i = 0; i < n; ++i) {
       lbm_ctx* h = hs[i];
-      if (h->t >= h->p.nsteps) continue;  // horizon reached
+      if (h->t >= stop[(size_t)i]) continue;  // horizon or this call's steps reached
       const int src = find_buf(h, h->t);
       int dst;
       lbm_status s = acquire_evict(h, h->t, &dst);
-      if (s) return batch_fail(hs[0], h, s);
+      if (s) return unwind(h, s);
       if (h->N >= kBatchAloneNodes) {
         s = launch_primal(h, src, dst, h->t, true, K_PRIMAL);  // folds its own objective
-        if (s) return batch_fail(hs[0], h, s);
+        if (s) return unwind(h, s);
         moved.push_back({h, src, dst, true});
         continue;
       }
@@ -937,13 +1078,13 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
       moved.push_back({h, src, dst, false});
       if (args.n == albm::kMaxBatch) {
         s = batch_launch(hs[0], args, blocks, false);
-        if (s) return s;
+        if (s) return unwind(hs[0], s);
         blocks = 0;
       }
     }
     if (args.n > 0) {
       lbm_status s = batch_launch(hs[0], args, blocks, false);
-      if (s) return s;
+      if (s) return unwind(hs[0], s);
     }
     for (auto& m : moved) {
       lbm_ctx* h = m.h;
@@ -963,14 +1104,36 @@ lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
   return LBM_OK;
 }
 
-lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k) {
+lbm_status lbm_batch_primal_step(const lbm_handle* hs, int n, int k) {
+  return batch_primal(hs, n, nullptr, k);
+}
+
+lbm_status lbm_batch_primal_steps(const lbm_handle* hs, int n, const int* ks) {
+  if (!ks) return LBM_ERR_ARG;
+  return batch_primal(hs, n, ks, 0);
+}
+
+// Batched adjoint steps; handle i stops at adjoint time stop[i] (0 at least).
+static lbm_status batch_adjoint(const lbm_handle* hs, int n, const int* ks, int kall) {
   lbm_status st = batch_check(hs, n);
   if (st) return st;
+  for (int i = 0; i < n; ++i) {
+    if (hs[i]->p.adjoint_mode != 0)
+      FAIL(hs[0], LBM_ERR_ARG, "batched adjoint steps need the unsteady adjoint (adjoint_mode 0)");
+    if ((ks ? ks[i] : kall) < 0) FAIL(hs[0], LBM_ERR_ARG, "negative step count");
+  }
   for (int i = 0; i < n; ++i)
     if (hs[i]->t_adj < 0) {
       lbm_status s = adjoint_start(hs[i]);
       if (s) return batch_fail(hs[0], hs[i], s);
     }
+  std::vector<int> stop((size_t)n);
+  int k = 0;
+  for (int i = 0; i < n; ++i) {
+    const int ki = ks ? ks[i] : kall;
+    stop[(size_t)i] = std::max(hs[i]->t_adj - ki, 0);
+    k = std::max(k, ki);
+  }
   static thread_local albm::BatchArgs args;
   for (int step = 0; step < k; ++step) {
     args.n = 0;
@@ -979,7 +1142,7 @@ lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k) {
     bool any = false;
     for (int i = 0; i < n; ++i) {
       lbm_ctx* h = hs[i];
-      if (h->t_adj <= 0) continue;  // adjoint finished
+      if (h->t_adj <= stop[(size_t)i]) continue;  // adjoint finished or this call's steps done
       const int nn = h->t_adj - 1;
       for (size_t b = 0; b < h->bufs.size(); ++b)
         if (h->buf_time[b] > nn) h->buf_time[b] = -1;
@@ -1025,6 +1188,15 @@ lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k) {
     if (!any) break;
   }
   return LBM_OK;
+}
+
+lbm_status lbm_batch_adjoint_step(const lbm_handle* hs, int n, int k) {
+  return batch_adjoint(hs, n, nullptr, k);
+}
+
+lbm_status lbm_batch_adjoint_steps(const lbm_handle* hs, int n, const int* ks) {
+  if (!ks) return LBM_ERR_ARG;
+  return batch_adjoint(hs, n, ks, 0);
 }
 
 lbm_status lbm_run(lbm_handle h) {
@@ -1145,6 +1317,21 @@ lbm_status lbm_check_finite(lbm_handle h, long long* count) {
   }
   *count = (long long)c;
   if (c) FAIL(h, LBM_ERR_NONFINITE, "%llu non-finite values in the state at time %d", c, h->t);
+  return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_handle h, void* stream) {
+  if (!h) return LBM_ERR_ARG;
+  cudaStream_t ns = (cudaStream_t)stream;
+  if (ns == h->stream) return LBM_OK;
+  // work already queued for this handle on its old stream comes first
+  cudaEvent_t ev = nullptr;
+  CK(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ns, ev, 0);
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "lbm_set_stream: %s", cudaGetErrorString(e));
+  h->stream = ns;
   return LBM_OK;
 }
 
@@ -1433,7 +1620,8 @@ static lbm_status mma_launch(lbm_ctx* h, const double* grad, int maximize, doubl
 
 lbm_status lbm_mma_update(lbm_handle h, int maximize, double move) {
   if (!h) return LBM_ERR_ARG;
-  if (h->oneshot || h->t_adj != 0)
+  const bool done = h->p.adjoint_mode == 1 ? (h->t_adj >= 0 && h->frozen_k > 0) : h->t_adj == 0;
+  if (h->oneshot || !done)
     FAIL(h, LBM_ERR_STATE, "MMA needs a completed adjoint (lbm_run) before the update");
   lbm_status s = mma_launch(h, h->grad, maximize, move);
   if (s) return s;

@@ -73,6 +73,22 @@ __device__ __forceinline__ void st(float* p, float v) {
 __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 
+// Fluid deviation of population i from its stored value and back.  16-bit
+// storage holds d_i - dev_off[i] (the deviation from the equilibrium at the
+// reference velocity, smaller than the deviation from rest in a channel
+// flowing near that velocity, so rounded with a smaller absolute error);
+// FP32 storage holds d_i itself.
+template <class S>
+__device__ __forceinline__ float dev_in(const KParams& P, int i, float raw) {
+  if constexpr (sizeof(S) == 2) return raw + P.dev_off[i];
+  else return raw;
+}
+template <class S>
+__device__ __forceinline__ float dev_out(const KParams& P, int i, float d) {
+  if constexpr (sizeof(S) == 2) return d - P.dev_off[i];
+  else return d;
+}
+
 // ---- periodic neighbourhood of one node ----------------------------------
 struct Geo {
   long long idx;
@@ -93,10 +109,12 @@ struct Geo {
 __device__ __forceinline__ Geo make_geo(const KParams& P, long long idx) {
   Geo g;
   g.idx = idx;
-  const long long r = idx / P.nx;
-  g.x = (int)(idx - r * P.nx);
-  g.z = (int)(r / P.ny);
-  g.y = (int)(r - (long long)g.z * P.ny);
+  // 32-bit index arithmetic (N < 2^31 is checked at creation)
+  const unsigned n = (unsigned)idx;
+  const unsigned r = fdiv(n, P.fd_nx);
+  g.x = (int)(n - r * (unsigned)P.nx);
+  g.z = (int)fdiv(r, P.fd_ny);
+  g.y = (int)(r - (unsigned)g.z * (unsigned)P.ny);
   const long long sxy = (long long)P.nx * P.ny;
   g.oxm = (g.x == 0) ? (P.nx - 1) : -1;
   g.oxp = (g.x == P.nx - 1) ? -(P.nx - 1) : 1;
@@ -152,11 +170,12 @@ struct Gather {
   static constexpr int Q = L::Q, QS = LS::Q;
   static constexpr int NSA = NS > 0 ? NS : 1;
   // f^n(x) from B^n: d_j = B_j(x - e_j), g_j = B_{Q+s QS+j}(x - e_j)
-  __device__ static __forceinline__ void pre(const Geo& geo, long long N, const S* __restrict__ B,
-                                             float* d, float (*g)[QS]) {
+  __device__ static __forceinline__ void pre(const KParams& P, const Geo& geo, long long N,
+                                             const S* __restrict__ B, float* d, float (*g)[QS]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-      d[i] = ld(B + (long long)i * N + geo.idx + geo.off(-L::ex(i), -L::ey(i), -L::ez(i)));
+      d[i] = dev_in<S>(P, i, ld(B + (long long)i * N + geo.idx +
+                                   geo.off(-L::ex(i), -L::ey(i), -L::ez(i))));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -183,12 +202,12 @@ __device__ __forceinline__ void primal_body(const KParams& P, const S* __restric
   if (idx < P.N) {
     const Geo geo = make_geo(P, idx);
     float d[Q], g[NSA][QS];
-    Gather<L, NS, S>::pre(geo, P.N, Bin, d, g);
+    Gather<L, NS, S>::pre(P, geo, P.N, Bin, d, g);
     const uint8_t type = flags[idx];
     const float th = theta[idx];
     Ops::template forward<OBJ>(P, type, th, geo.y, d, g, OBJ != 0 && obj != nullptr, o1, o2);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, d[i]);
+    for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, dev_out<S>(P, i, d[i]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -268,9 +287,11 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
   double o1 = 0.0, o2 = 0.0;
   const int hx = P.nx >> 1;
   if (pair < P.N / 2) {
-    const long long row = pair / hx;
-    const int x = 2 * (int)(pair - row * hx);
-    const int y = (int)(row % P.ny), z = (int)(row / P.ny);
+    const unsigned rw = fdiv((unsigned)pair, P.fd_hx);
+    const long long row = rw;
+    const int x = 2 * (int)((unsigned)pair - rw * (unsigned)hx);
+    const int z = (int)fdiv(rw, P.fd_ny);
+    const int y = (int)(rw - (unsigned)z * (unsigned)P.ny);
     const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? P.nz - 1 : z - 1, zp = z == P.nz - 1 ? 0 : z + 1;
     auto rowoff = [&](int ey, int ez) -> long long {  // source row of shift (ey, ez)
@@ -280,9 +301,12 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
     };
     float da[Q], db[Q], ga[NSA][QS], gb[NSA][QS];
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
+    for (int i = 0; i < Q; ++i) {
       gather_pair<S>(Bin + (long long)i * P.N + rowoff(L::ey(i), L::ez(i)), L::ex(i), x, P.nx, da[i],
                      db[i]);
+      da[i] = dev_in<S>(P, i, da[i]);
+      db[i] = dev_in<S>(P, i, db[i]);
+    }
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -295,7 +319,8 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
     Ops::template forward<OBJ>(P, ta, th.x, y, da, ga, OBJ != 0 && obj != nullptr, o1, o2);
     Ops::template forward<OBJ>(P, tb, th.y, y, db, gb, OBJ != 0 && obj != nullptr, o1, o2);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Pair<S>::st(Bout + (long long)i * P.N + idx, da[i], db[i]);
+    for (int i = 0; i < Q; ++i)
+      Pair<S>::st(Bout + (long long)i * P.N + idx, dev_out<S>(P, i, da[i]), dev_out<S>(P, i, db[i]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -305,8 +330,14 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
   if (OBJ != 0 && obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
 }
 
+// resident blocks of the paired 16-bit primal (128 threads): 5 keeps it
+// within 96 registers without spills for up to one scalar lattice; two
+// scalars spill at 5 and keep 4
+#ifndef ALBM_PAIR_MINB
+#define ALBM_PAIR_MINB 5
+#endif
 template <class L, int NS, bool MRT, class S, int OBJ>
-__global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK, 4) primal_pair_kernel(
+__global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK, NS >= 2 ? 4 : ALBM_PAIR_MINB) primal_pair_kernel(
     KParams P, const S* __restrict__ Bin, S* __restrict__ Bout, const float* __restrict__ theta,
     const uint8_t* __restrict__ flags, double* __restrict__ obj) {
   primal_pair_body<L, NS, MRT, S, OBJ>(P, Bin, Bout, theta, flags, obj,
@@ -330,7 +361,7 @@ __global__ void __launch_bounds__(256) objective_kernel(KParams P, const S* __re
     if (relevant) {
       const Geo geo = make_geo(P, idx);
       float d[Q], g[NSA][QS];
-      Gather<L, NS, S>::pre(geo, P.N, Bin, d, g);
+      Gather<L, NS, S>::pre(P, geo, P.N, Bin, d, g);
       Ops::forward(P, type, theta[idx], geo.y, d, g, true, o1, o2);
     }
   }
@@ -341,19 +372,44 @@ __global__ void __launch_bounds__(256) objective_kernel(KParams P, const S* __re
 // ---------------------------------------------------------------------------
 // adjoint step: lambda^n(x) from lambda^{n+1}(x + e_j) and f^n(x)
 // ---------------------------------------------------------------------------
-// One-shot design update fused into the adjoint step (Sec. 3.3, Eq.
-// gradient:update with the penalty of Eq. P): active when theta_out is set.
-// The node's gradient estimate g overwrites grad (instead of accumulating)
-// and, on design nodes, theta_out = clamp(theta + zeta (sign g - penalty
-// (1 - 2 theta)), 0, 1) in FP32.  Each thread reads and writes only its own
-// node's theta, after its last read of it.
+// Gradient modes of the adjoint step.  Unsteady adjoint (default): the
+// theta terms are added to grad.  Fixed-point ALBS at a held state (Sec.
+// 2.2, Eq. adjoint:iteration; overwrite set): the node's gradient estimate
+// g of Eq. adjoint:derivative from the iterate this step consumes
+// overwrites grad.  One-shot design update fused into the step (Sec. 3.3,
+// Eq. gradient:update with the penalty of Eq. P; theta_out set): g
+// overwrites grad and, on design nodes, theta_out = clamp(theta + zeta
+// (sign g - penalty (1 - 2 theta)), 0, 1) in FP32.  Each thread reads and
+// writes only its own node's theta, after its last read of it.
 struct OneShot {
   const uint8_t* design;
   float* theta_out;
   float zeta, penalty, sign;
+  int overwrite;
 };
 
-template <class L, int NS, bool MRT, class S, int SRC = 2>
+// lambda^{n+1} prefetch of the single-instance adjoint (ALBM_ADJ_CPASYNC):
+// each thread copies its own gathers into its column of a shared-memory
+// block with 4-byte cp.async right after the node index is known, so they
+// travel while the forward quantities are recomputed, and reads them back
+// after waiting for its own copies (no barrier: no thread reads another's).
+#ifndef ALBM_ADJ_CPASYNC
+#define ALBM_ADJ_CPASYNC 0
+#endif
+__device__ __forceinline__ void lam_cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void lam_cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void lam_cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <class L, int NS, bool MRT, class S, int SRC = 2, bool PREF = false>
 __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __restrict__ lam_in,
                                              const S* __restrict__ Bn, float* __restrict__ lam_out,
                                              const float* __restrict__ theta,
@@ -366,14 +422,41 @@ __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __re
   constexpr int Q = Ops::Q, QS = Ops::QS, NSA = Ops::NSA;
   if (idx >= P.N) return;
   const Geo geo = make_geo(P, idx);
+  [[maybe_unused]] float* sl = nullptr;
+  if constexpr (PREF) {
+    extern __shared__ float adj_lam_smem[];
+    sl = adj_lam_smem + threadIdx.x;
+    if (has_next) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        lam_cp_async4(sl + i * blockDim.x,
+                      lam_in + (long long)i * P.N + idx + geo.off(L::ex(i), L::ey(i), L::ez(i)));
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int i = 0; i < QS; ++i)
+          lam_cp_async4(sl + (Q + s * QS + i) * blockDim.x,
+                        lam_in + (long long)(Q + s * QS + i) * P.N + idx +
+                            geo.off(LS::ex(i), LS::ey(i), LS::ez(i)));
+      lam_cp_async_commit();
+    }
+  }
   float d[Q], g[NSA][QS];
-  Gather<L, NS, S>::pre(geo, P.N, Bn, d, g);
+  Gather<L, NS, S>::pre(P, geo, P.N, Bn, d, g);
   const uint8_t type = flags[idx];
   // outlet mean of scalar 0 at this step (variance objective)
   const float cbar = stat_n != nullptr ? (float)(stat_n[0] * (double)P.inv_A_out) : 0.0f;
   // lambda^{n+1}_j(x + e_j), or zero for the first (source-only) step
   auto load = [&](float* a, float (*b)[QS]) {
-    if (has_next) {
+    if (has_next && PREF) {
+      lam_cp_async_wait_all();
+#pragma unroll
+      for (int i = 0; i < Q; ++i) a[i] = sl[i * blockDim.x];
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+#pragma unroll
+        for (int i = 0; i < QS; ++i) b[s][i] = sl[(Q + s * QS + i) * blockDim.x];
+    } else if (has_next) {
 #pragma unroll
       for (int i = 0; i < Q; ++i)
         a[i] = __ldg(lam_in + (long long)i * P.N + idx + geo.off(L::ex(i), L::ey(i), L::ez(i)));
@@ -403,10 +486,10 @@ __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __re
 #pragma unroll
     for (int i = 0; i < QS; ++i) st(lam_out + (long long)(Q + s * QS + i) * P.N + idx, lamg[s][i]);
   const bool has_theta = type == FLUID || type == INLET || type == OUTLET;
-  if (os.theta_out != nullptr) {
+  if (os.theta_out != nullptr || os.overwrite) {
     const float gk = has_theta ? dth : 0.0f;
     grad[idx] = (double)gk;
-    if (os.design[idx]) {
+    if (os.theta_out != nullptr && os.design[idx]) {
       const float tn = th + os.zeta * (os.sign * gk - os.penalty * (1.0f - 2.0f * th));
       os.theta_out[idx] = fminf(fmaxf(tn, 0.0f), 1.0f);
     }
@@ -427,8 +510,9 @@ __global__ void __launch_bounds__(ALBM_ADJ_BLOCK, SRC == 2 ? ALBM_ADJOINT_MINB :
                                                       double* __restrict__ grad, float ws,
                                                       const double* __restrict__ stat_n,
                                                       int has_next, OneShot os) {
-  adjoint_body<L, NS, MRT, S, SRC>(P, lam_in, Bn, lam_out, theta, flags, grad, ws, stat_n, has_next,
-                                   (long long)blockIdx.x * blockDim.x + threadIdx.x, os);
+  adjoint_body<L, NS, MRT, S, SRC, ALBM_ADJ_CPASYNC != 0>(
+      P, lam_in, Bn, lam_out, theta, flags, grad, ws, stat_n, has_next,
+      (long long)blockIdx.x * blockDim.x + threadIdx.x, os);
 }
 
 // ---------------------------------------------------------------------------
@@ -463,10 +547,16 @@ struct BatchArgs {
 // kernel parameters may take up to 32764 bytes (sm_70 and newer)
 static_assert(sizeof(BatchArgs) <= 32000, "instance table exceeds the kernel parameter space");
 
+// the instance whose block range holds this block: binary search over the
+// ascending block_begin of the table
 __device__ __forceinline__ int batch_instance(const BatchArgs& a) {
-  int lo = 0;
-  for (int i = 1; i < a.n; ++i)
-    if ((long long)blockIdx.x >= a.inst[i].block_begin) lo = i;
+  int lo = 0, hi = a.n - 1;
+  const long long b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b >= a.inst[mid].block_begin) lo = mid;
+    else hi = mid - 1;
+  }
   return lo;
 }
 
@@ -525,7 +615,7 @@ __global__ void export_kernel(KParams P, const S* __restrict__ B, float* __restr
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const long long src = post ? idx : idx + geo.off(-L::ex(i), -L::ey(i), -L::ez(i));
-    out[(long long)i * P.N + idx] = L::w(i) + ld(B + (long long)i * P.N + src);
+    out[(long long)i * P.N + idx] = L::w(i) + dev_in<S>(P, i, ld(B + (long long)i * P.N + src));
   }
 #pragma unroll
   for (int s = 0; s < NS; ++s)
@@ -548,7 +638,7 @@ __global__ void import_kernel(KParams P, const float* __restrict__ in, S* __rest
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const long long src = idx + geo.off(L::ex(i), L::ey(i), L::ez(i));
-    st(B + (long long)i * P.N + idx, __ldg(in + (long long)i * P.N + src) - L::w(i));
+    st(B + (long long)i * P.N + idx, dev_out<S>(P, i, __ldg(in + (long long)i * P.N + src) - L::w(i)));
   }
 #pragma unroll
   for (int s = 0; s < NS; ++s)
@@ -558,6 +648,19 @@ __global__ void import_kernel(KParams P, const float* __restrict__ in, S* __rest
       const long long src = idx + geo.off(LS::ex(i), LS::ey(i), LS::ez(i));
       st(B + m * P.N + idx, __ldg(in + m * P.N + src));
     }
+}
+
+// the rest state f^0 = w (deviation 0), fluid rows as stored, scalars 0
+template <class L, int NS, class S>
+__global__ void rest_kernel(KParams P, S* __restrict__ B) {
+  using LS = typename ScalarOf<L>::type;
+  constexpr int Q = L::Q, QS = LS::Q;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.N) return;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) st(B + (long long)i * P.N + idx, dev_out<S>(P, i, 0.0f));
+#pragma unroll
+  for (int m = Q; m < Q + NS * QS; ++m) st(B + (long long)m * P.N + idx, 0.0f);
 }
 
 template <class S>
@@ -609,6 +712,7 @@ struct KernelSet {
   cudaError_t (*exportf)(const KParams&, const StepArgs&, cudaStream_t);
   cudaError_t (*importf)(const KParams&, const StepArgs&, cudaStream_t);
   cudaError_t (*nonfinite)(const KParams&, const StepArgs&, int M, cudaStream_t);
+  cudaError_t (*rest)(const KParams&, const StepArgs&, cudaStream_t);
   cudaError_t (*primal_batch)(const BatchArgs&, long long blocks, cudaStream_t);
   cudaError_t (*adjoint_batch)(const BatchArgs&, long long blocks, cudaStream_t);
   cudaError_t (*primal_tiles)(const KParams&, const StepArgs&, cudaStream_t);
@@ -674,8 +778,11 @@ struct Launch {
     auto k = sk == 0 ? adjoint_kernel<L, NS, MRT, S, 0>
              : sk == 1 ? adjoint_kernel<L, NS, MRT, S, 1>
                        : adjoint_kernel<L, NS, MRT, S, 2>;
-    k<<<nb, ALBM_ADJ_BLOCK, 0, st>>>(P, a.lam_in, (const S*)a.Bin, a.lam_out, a.theta, a.flags,
-                                     a.grad, a.ws, a.stat_n, a.has_next, a.os);
+    const size_t smem = ALBM_ADJ_CPASYNC ? sizeof(float) * (size_t)(L::Q + NS * ScalarOf<L>::type::Q) *
+                                               ALBM_ADJ_BLOCK
+                                         : 0;
+    k<<<nb, ALBM_ADJ_BLOCK, smem, st>>>(P, a.lam_in, (const S*)a.Bin, a.lam_out, a.theta, a.flags,
+                                        a.grad, a.ws, a.stat_n, a.has_next, a.os);
     return cudaGetLastError();
   }
   static cudaError_t exportf(const KParams& P, const StepArgs& a, cudaStream_t st) {
@@ -684,6 +791,10 @@ struct Launch {
   }
   static cudaError_t importf(const KParams& P, const StepArgs& a, cudaStream_t st) {
     import_kernel<L, NS, S><<<blocks(P), kBlock, 0, st>>>(P, a.fin, (S*)a.Bout);
+    return cudaGetLastError();
+  }
+  static cudaError_t rest(const KParams& P, const StepArgs& a, cudaStream_t st) {
+    rest_kernel<L, NS, S><<<blocks(P), kBlock, 0, st>>>(P, (S*)a.Bout);
     return cudaGetLastError();
   }
   static cudaError_t nonfinite(const KParams& P, const StepArgs& a, int M, cudaStream_t st) {
@@ -765,7 +876,7 @@ struct Launch {
     return (threads + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK;
   }
   static KernelSet set() {
-    return KernelSet{&primal, &objective, &adjoint, &exportf, &importf, &nonfinite,
+    return KernelSet{&primal, &objective, &adjoint, &exportf, &importf, &nonfinite, &rest,
                      &primal_batch, &adjoint_batch, &primal_tiles, &adjoint_tiles,
                      &primal_async, &adjoint_async, &primal_partials, (int)sizeof(S)};
   }

@@ -235,6 +235,9 @@ extern "C" lbm_status lbm_state_objective_noalloc(const lbm_params* pp, const fl
   P.nz = p.nz;
   P.nscal = p.nscalars;
   P.N = N;
+  P.fd_nx = albm::make_fastdiv((unsigned)p.nx);
+  P.fd_ny = albm::make_fastdiv((unsigned)p.ny);
+  P.fd_hx = albm::make_fastdiv((unsigned)(p.nx / 2 > 0 ? p.nx / 2 : 1));
   const double omega = 1.0 / p.tau;
   P.omega = (float)omega;
   P.one_m_omega = (float)(1.0 - omega);

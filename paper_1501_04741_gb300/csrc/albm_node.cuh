@@ -63,6 +63,11 @@ __host__ __device__ inline int obj_kind(bool active, int objective) {
 #ifndef ALBM_C_LOOP
 #define ALBM_C_LOOP 0
 #endif
+// fluid collision as two equilibria per population (the direct form of the
+// operator) instead of the polynomial form of NodeOps::collide_fluid
+#ifndef ALBM_COLLIDE_DIRECT
+#define ALBM_COLLIDE_DIRECT 0
+#endif
 // MRT: keep the conserved moments in the rank-one operator.  They act on
 // f - f_eq(rho, u), whose density and momentum vanish, and in the adjoint on
 // a vector that (I - d f_eq / d f)^T annihilates along them, so by default
@@ -70,6 +75,36 @@ __host__ __device__ inline int obj_kind(bool active, int objective) {
 #ifndef ALBM_MRT_CONSERVED
 #define ALBM_MRT_CONSERVED 0
 #endif
+
+// Division of a 32-bit unsigned n by a divisor d that is fixed for the
+// problem, by a multiply-high and two shifts (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, Fig.
+// 4.1: l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n -
+// t) >> min(l, 1))) >> max(l - 1, 0) with t = mulhi(m, n); exact for every
+// 32-bit n and d >= 1).  Replaces the 64-bit division of a node index by
+// the row length, which costs tens of instructions per node.
+struct FastDiv {
+  unsigned m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+  unsigned l = 0;
+  while (l < 32 && (1ull << l) < (unsigned long long)d) ++l;
+  FastDiv f;
+  f.m = (unsigned)((((1ull << 32) * ((1ull << l) - (unsigned long long)d)) / d) + 1ull);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
+__host__ __device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+  const unsigned t = __umulhi(f.m, n);
+#else
+  const unsigned t = (unsigned)(((unsigned long long)f.m * n) >> 32);
+#endif
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
 
 // Constants of one problem, passed by value to every kernel.
 struct KParams {
@@ -87,6 +122,12 @@ struct KParams {
   float inv_A_in, inv_A_out;
   float mrt_diag;
   float mrt_r[19];
+  // 16-bit storage: stored value = d_i - dev_off[i], with dev_off[i] =
+  // f_eq,i(1, u_ref) - w_i the equilibrium deviation at the reference
+  // velocity (zero for FP32 storage)
+  float dev_off[19];
+  // n / nx, n / ny and n / (nx / 2) for node, row and pair indices (N < 2^31)
+  FastDiv fd_nx, fd_ny, fd_hx;
 };
 
 // MRT coefficients of NodeOps::mrt_op for rates omega (stress moments),
@@ -100,6 +141,18 @@ inline void fill_mrt(double omega, double s_other, KParams& k) {
     for (int i = 0; i < L::Q; ++i) D += double(L::U(j, i)) * double(L::U(j, i));
     if (L::stress(j)) k.mrt_r[j] = (float)((s_other - omega) / D);
     if (L::conserved(j)) k.mrt_r[j] = (float)(s_other / D);
+  }
+}
+
+// Reference offsets of 16-bit storage: dev_off[i] = f_eq,i(1, u_ref) - w_i =
+// w_i (3 e.u + 4.5 (e.u)^2 - 1.5 u.u) at the reference velocity u_ref
+template <class L>
+inline void fill_dev_off(const double* u_ref, KParams& k) {
+  for (int j = 0; j < 19; ++j) k.dev_off[j] = 0.f;
+  const double uu = u_ref[0] * u_ref[0] + u_ref[1] * u_ref[1] + u_ref[2] * u_ref[2];
+  for (int i = 0; i < L::Q; ++i) {
+    const double eu = L::ex(i) * u_ref[0] + L::ey(i) * u_ref[1] + L::ez(i) * u_ref[2];
+    k.dev_off[i] = (float)(double(L::w(i)) * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
   }
 }
 
@@ -366,6 +419,78 @@ struct NodeOps {
   }
 
   // -------------------------------------------------------------------------
+  // Fluid collision of a node in polynomial form.  With r the factor that
+  // BGK keeps of the non-equilibrium part (1 - omega), or that MRT keeps of
+  // the moments outside the stress set (1 - s_other),
+  //   deq(v) + r (d - deq(u))                               (BGK)
+  //   deq(v) + r (d - deq(u)) + sum_k U_k m_k               (MRT, k stress)
+  // where m_k = c_k U_k.(d - deq(u)).  Because deq_i(rho, u) = w_i (drho +
+  // rho (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)) is a quadratic polynomial in e_i,
+  //   deq_i(v) - r deq_i(u) = w_i (K0 + e_i.A + e_i^T Pi e_i),
+  //   K0 = (1 - r) drho - 1.5 rho (v.v - r u.u),   A = 3 rho (v - r u),
+  //   Pi = 4.5 rho (v v^T - r u u^T),
+  // a handful of node constants instead of two equilibria per population;
+  // the stress moments of deq(u) are rho 4.5 u^T M_k u with the constant
+  // weighted second moments M_k = sum_i w_i U_ki e_i e_i^T (its zeroth and
+  // first weighted moments vanish for the stress rows).  Same operator as
+  // the direct form (ALBM_COLLIDE_DIRECT), up to rounding.
+  // -------------------------------------------------------------------------
+  __device__ static __forceinline__ void collide_fluid(const KParams& P, float* d, float rho,
+                                                       float drho, const float* u, const float* v,
+                                                       float uu, float vv) {
+    const float r = MRT ? P.mrt_diag : P.one_m_omega;
+    const float K0 = (1.0f - r) * drho - 1.5f * rho * (vv - r * uu);
+    float A[3], Pm[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      A[a] = 3.0f * rho * (v[a] - r * u[a]);
+#pragma unroll
+      for (int b = a; b < 3; ++b) Pm[a][b] = 4.5f * rho * (v[a] * v[b] - r * (u[a] * u[b]));
+    }
+    float mk[L::NMOM];
+    if constexpr (MRT) {
+      // stress moments of d - deq(u), weighted by c_k
+#pragma unroll
+      for (int k = 0; k < L::NMOM; ++k) {
+        mk[k] = 0.0f;
+        if (!L::stress(k)) continue;
+        float a = 0.0f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+          if (L::U(k, i) != 0) a += float(L::U(k, i)) * d[i];
+        float eq = 0.0f;
+#pragma unroll
+        for (int p_ = 0; p_ < 3; ++p_)
+#pragma unroll
+          for (int q_ = 0; q_ < 3; ++q_)
+            if (UW2(k, p_, q_) != 0) eq += (float(UW2(k, p_, q_)) * (4.5f / 36.0f)) * (u[p_] * u[q_]);
+        mk[k] = P.mrt_r[k] * (a - rho * eq);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
+      float quad = K0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b)
+          if (e[a] * e[b] != 0) quad += float((a == b ? 1 : 2) * e[a] * e[b]) * Pm[a][b];
+      float lin = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (e[a] != 0) lin += float(e[a]) * A[a];
+      float y = r * d[i] + L::w(i) * (quad + lin);
+      if constexpr (MRT) {
+#pragma unroll
+        for (int k = 0; k < L::NMOM; ++k)
+          if (L::stress(k) && L::U(k, i) != 0) y += float(L::U(k, i)) * mk[k];
+      }
+      d[i] = y;
+    }
+  }
+
+  // -------------------------------------------------------------------------
   // Forward: W^x applied to d (fluid deviations) and g (scalars) in place.
   // obj1/obj2 receive this node's objective terms F^x(f^n(x)).  OBJ is the
   // objective form compiled in (see obj_kind): 0 none, 1 outlet/inlet
@@ -412,6 +537,7 @@ struct NodeOps {
     float v[3] = {G * u[0] + P.gx, G * u[1] + P.gy, G * u[2] + P.gz};
     const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const float vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+#if ALBM_COLLIDE_DIRECT
     if (MRT) {
       float neq[Q];
 #pragma unroll
@@ -426,6 +552,9 @@ struct NodeOps {
         d[i] = deq(i, rho, drho, v, vv) + P.one_m_omega * (d[i] - deq(i, rho, drho, u, uu));
       }
     }
+#else
+    collide_fluid(P, d, rho, drho, u, v, uu, vv);
+#endif
     if (NS == 0) return;
     float om, dom;
     scalar_rate<LS>(P, th, om, dom);

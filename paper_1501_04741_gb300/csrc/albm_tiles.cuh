@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(TX) primal_tiles_kernel(KParams P, const S* __
     const S* sb = stage[sg];
     float d[Q], g[NSA][QS];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = to_f(sb[i * W + H + lx - L::ex(i)]);
+    for (int i = 0; i < Q; ++i) d[i] = dev_in<S>(P, i, to_f(sb[i * W + H + lx - L::ex(i)]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(TX) primal_tiles_kernel(KParams P, const S* __
     double o1 = 0.0, o2 = 0.0;
     Ops::forward(P, flags[idx], theta[idx], y, d, g, obj != nullptr, o1, o2);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, d[i]);
+    for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, dev_out<S>(P, i, d[i]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(TX) adjoint_tiles_kernel(
     const float* ls = reinterpret_cast<const float*>(base[sg] + (size_t)M * W * sizeof(S));
     float d[Q], g[NSA][QS];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = to_f(fs[i * W + H + lx - L::ex(i)]);
+    for (int i = 0; i < Q; ++i) d[i] = dev_in<S>(P, i, to_f(fs[i * W + H + lx - L::ex(i)]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(TX) primal_async_kernel(KParams P, const S* __
     const S* sb = stage[sg];
     float d[Q], g[NSA][QS];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = to_f(sb[i * W + H + lx - L::ex(i)]);
+    for (int i = 0; i < Q; ++i) d[i] = dev_in<S>(P, i, to_f(sb[i * W + H + lx - L::ex(i)]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(TX) primal_async_kernel(KParams P, const S* __
     double o1 = 0.0, o2 = 0.0;
     Ops::forward(P, flags[idx], theta[idx], y, d, g, obj != nullptr, o1, o2);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, d[i]);
+    for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, dev_out<S>(P, i, d[i]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(TX) adjoint_async_kernel(
     const float* ls = reinterpret_cast<const float*>(base[sg] + (size_t)M * W * sizeof(S));
     float d[Q], g[NSA][QS];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = to_f(fs[i * W + H + lx - L::ex(i)]);
+    for (int i = 0; i < Q; ++i) d[i] = dev_in<S>(P, i, to_f(fs[i * W + H + lx - L::ex(i)]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll

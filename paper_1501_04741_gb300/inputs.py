@@ -65,6 +65,8 @@ class Problem:
     precision: str = "fp32"          # population storage on the GPU: fp32 | bf16 | fp16
     ckpt_every: int = 0              # level-1 checkpoint stride of the adjoint schedule
     kernel: str = "auto"             # GPU step kernels: auto | plain | tiles (staged rows)
+    adjoint_mode: str = "unsteady"   # "unsteady" (exact gradient over the horizon) | "frozen"
+    #                                  (the paper's fixed-point ALBS at f^N, Sec. 2.2)
 
     @property
     def n_nodes(self) -> int:

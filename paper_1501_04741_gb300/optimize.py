@@ -79,10 +79,19 @@ class MMAResult:
 
 
 def mma(P: Problem, theta0, iters: int, *, maximize: bool = True, move: float = 0.5,
-        design=None, stream=None) -> MMAResult:
-    """The MMA design loop of Sec. 3.3: per iteration a full solve (primal,
-    unsteady adjoint, dJ/dtheta) and one MMA update of theta, all in the
-    library (``lbm_run``, ``lbm_mma_update``)."""
+        design=None, stream=None, adjoint: str = "unsteady") -> MMAResult:
+    """The MMA design loop of Sec. 3.3: per iteration a full solve and one MMA
+    update of theta, all in the library (``lbm_run``, ``lbm_mma_update``).
+
+    ``adjoint="unsteady"``: the solve is the N-step primal and its exact
+    unsteady adjoint.  ``adjoint="frozen"``: the paper's schedule, the
+    N-step primal (run until the flow has converged) followed by the same
+    number of ALBS iterations at its final state (Sec. 3.3), whose gradient
+    is that of the stationary objective F(f^N)."""
+    if adjoint not in ("unsteady", "frozen"):
+        raise ValueError(f"unknown adjoint schedule {adjoint!r}")
+    if adjoint == "frozen":
+        P = P.replace(adjoint_mode="frozen", obj_window=0)
     with Solver(P, theta0, stream=stream) as s:
         s.set_design(design)
         s.mma_reset()

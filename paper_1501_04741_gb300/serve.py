@@ -13,7 +13,11 @@ steps, gradient).  The server
   collision, scalars, storage) and phase (primal / adjoint) and advances each
   group by up to ``steps_per_tick`` steps with batched launches (one kernel
   per step for the whole group), so requests that arrive while others run
-  join the next tick and their work overlaps on the device;
+  join the next tick and their work overlaps on the device; each group
+  launches on its own CUDA stream (a request moving between groups carries
+  the order of its queued work along, ``Solver.set_stream``), so the
+  groups' launches also overlap one another, and the tick waits for all
+  group streams at its end;
 * retires finished requests (J and dJ/dtheta copied out), frees their
   memory and admits from the queue again.
 
@@ -38,30 +42,51 @@ from .inputs import Problem
 Q_FLUID = {"D2Q9": 9, "D3Q19": 19}
 Q_SCALAR = {"D2Q9": 9, "D3Q19": 7}
 STORAGE = {"fp32": 4, "bf16": 2, "fp16": 2}
+OOM = 2          # LBM_ERR_OOM
 
 
 def densities(P: Problem) -> int:
     return Q_FLUID[P.lattice] + P.nscalars * Q_SCALAR[P.lattice]
 
 
+# device allocations are charged in whole 2 MiB pages, the granularity of
+# cudaMalloc's mappings (the library carves small states out of larger
+# slabs, so the pool itself costs its bytes plus at most one page)
+ALLOC_GRANULE = 2 << 20
+
+
+def _alloc(nbytes: float) -> int:
+    return int(-(-int(nbytes) // ALLOC_GRANULE) * ALLOC_GRANULE)
+
+
 def state_bytes(P: Problem) -> int:
     return densities(P) * P.n_nodes * STORAGE[P.precision]
+
+
+def _stride(P: Problem) -> int:
+    """Bytes one pool state occupies (its size rounded up to 256)."""
+    return -(-state_bytes(P) // 256) * 256
 
 
 def pool_states(P: Problem, max_states: int = 48, pool_cap_bytes: float = 0.0) -> int:
     """States the request's pool may hold: the whole trajectory when it is
     short, else the larger of ``max_states`` and what ``pool_cap_bytes``
     allows (level-1 checkpoints plus recompute slots)."""
-    cap = max(int(max_states), int(pool_cap_bytes // max(state_bytes(P), 1)))
+    cap = max(int(max_states), int(pool_cap_bytes // max(_stride(P), 1)))
     return int(min(P.nsteps + 2, max(8, cap)))
 
 
 def request_bytes(P: Problem, max_states: int = 48, pool_cap_bytes: float = 0.0) -> int:
-    """Device bytes of one resident request (the admission byte model)."""
+    """Device bytes of one resident request (the admission byte model): the
+    state pool, the two adjoint buffers, gradient, theta, flags, the
+    objective record and per-block partials, each in whole allocation
+    pages, plus the gradient copied out through torch at retirement."""
     N, M = P.n_nodes, densities(P)
-    pool = pool_states(P, max_states, pool_cap_bytes) * state_bytes(P)
-    lam = 2 * M * N * 4
-    return int(pool + lam + 8 * N + 5 * N + 16 * 65 * (P.nsteps + 1) + (1 << 20))
+    pool = pool_states(P, max_states, pool_cap_bytes) * _stride(P) + ALLOC_GRANULE
+    lam = 2 * _alloc(M * N * 4)
+    small = (_alloc(8 * N) + _alloc(4 * N) + _alloc(N) + _alloc(16 * (P.nsteps + 1))
+             + _alloc(16 * (N // 64 + 1)) + 2 * ALLOC_GRANULE)
+    return int(pool + lam + small + _alloc(8 * N))
 
 
 @dataclasses.dataclass
@@ -102,7 +127,7 @@ def _percentiles(lat):
 
 
 class Server:
-    def __init__(self, reserve_bytes: float = 2 << 30, capacity_bytes: float | None = None,
+    def __init__(self, reserve_bytes: float = 4 << 30, capacity_bytes: float | None = None,
                  steps_per_tick: int = 200, work_per_tick: float = 2e7, max_states: int = 48,
                  pool_fraction: float = 0.25, stream=None,
                  mem_get_info=None, keep_gradients: bool = True, solver_factory=None,
@@ -117,7 +142,10 @@ class Server:
         self.stream = stream
         info = mem_get_info or torch.cuda.mem_get_info
         free, _ = info()
-        self.capacity = float(capacity_bytes) if capacity_bytes is not None else free - reserve_bytes
+        # the device does not hand out every byte cudaMemGetInfo reports free:
+        # keep the larger of the reserve and 8 % of it back
+        self.capacity = (float(capacity_bytes) if capacity_bytes is not None
+                         else free - max(float(reserve_bytes), 0.08 * free))
         self.steps_per_tick = int(steps_per_tick)       # cap of steps per request per tick
         self.work_per_tick = float(work_per_tick)       # node-steps per request per tick
         self.max_states = int(max_states)
@@ -129,6 +157,7 @@ class Server:
         self.finished = []
         self.launches = 0
         self.max_resident = 0
+        self.group_streams = {}      # (family, phase) -> stream of that group
 
     # ---- admission ------------------------------------------------------------
     def submit(self, req: Request):
@@ -148,7 +177,7 @@ class Server:
                 break                       # wait for memory to free up (FIFO)
             self.queue.popleft()
             try:
-                budget = pool_states(req.P, self.max_states, self.pool_cap) * state_bytes(req.P)
+                budget = pool_states(req.P, self.max_states, self.pool_cap) * _stride(req.P)
                 req.solver = self.solver_factory(req.P, req.theta, stream=self.stream,
                                                  mem_budget=budget)
             except (AlbmError, RuntimeError) as e:
@@ -168,16 +197,58 @@ class Server:
             s = r.solver
             phase = "primal" if s.time < r.P.nsteps and s.adjoint_time < 0 else "adjoint"
             groups.setdefault((_family(r.P), phase), []).append(r)
+        used = []
         for (fam, phase), rs in groups.items():
+            st = self._group_stream((fam, phase))
+            if st is not None:
+                used.append(st)
+                for r in rs:
+                    if hasattr(r.solver, "set_stream"):
+                        r.solver.set_stream(st)
             # equal node-updates per request per tick: small requests take
             # many steps while a large one takes few, so they do not wait on it
             ks = [max(1, min(self.steps_per_tick, int(self.work_per_tick / r.P.n_nodes)))
                   for r in rs]
             fn = self.primal_fn if phase == "primal" else self.adjoint_fn
-            for j in range(max(ks)):
-                ss = [r.solver for r, k in zip(rs, ks) if k > j]
-                fn(ss, 1)
-                self.launches += (len(ss) + 63) // 64
+            # one call per group: the library loops over the steps, each
+            # launch covering the requests that still have steps this tick
+            try:
+                fn([r.solver for r in rs], ks)
+                self.launches += max(ks) * ((len(rs) + 63) // 64)
+            except AlbmError as e:
+                if e.code != OOM:
+                    raise
+                # a state pool could not grow: finish the tick's steps of the
+                # group's requests one by one, failing those that still run
+                # out of memory
+                for r, k in zip(rs, ks):
+                    try:
+                        fn([r.solver], [k])
+                        self.launches += k
+                    except AlbmError as e1:
+                        if e1.code != OOM:
+                            raise
+                        self._fail(r, "out of device memory")
+        for st in used:
+            st.synchronize()
+
+    def _group_stream(self, key):
+        """The stream of one (family, phase) group; None on a fake device."""
+        if self.stream is None:
+            return None
+        if key not in self.group_streams:
+            self.group_streams[key] = torch.cuda.Stream()
+        return self.group_streams[key]
+
+    def _fail(self, r: Request, msg: str):
+        """Retire a resident request with an error and release its memory."""
+        r.error = msg
+        r.done = time.perf_counter() - self._t0
+        r.solver.close()
+        r.solver = None
+        self.committed -= r.bytes
+        self.active.remove(r)
+        self.finished.append(r)
 
     def _retire(self, now: float):
         still = []
@@ -238,8 +309,6 @@ class Server:
                         time.sleep(min(wait, 0.05))
                 continue
             self._tick()
-            if self.stream is not None:
-                self.stream.synchronize()
             self._retire(time.perf_counter() - self._t0)
             if on_tick is not None:
                 on_tick(self)

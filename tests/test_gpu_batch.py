@@ -124,3 +124,31 @@ def test_solves_are_bit_reproducible():
     a = _alone(P, th)
     b = _alone(P, th)
     assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+def test_per_handle_step_counts_match_single_steps():
+    # lbm_batch_primal_steps / lbm_batch_adjoint_steps with a different count
+    # per handle reach the same states as stepping each handle alone
+    from paper_1501_04741_gb300.albm import Solver, batch_adjoint_step, batch_primal_step
+    Ps = [inputs.channel2d(dims=(40 + 8 * i, 21, 1), design=(8, 30, 4, 17, 0, 1), nsteps=50,
+                           force=(1e-4, 0.0, 0.0)) for i in range(3)]
+    ths = [torch.from_numpy(inputs.theta_uniform(P, 20 + i).reshape(-1)).cuda()
+           for i, P in enumerate(Ps)]
+    batch = [Solver(P, th) for P, th in zip(Ps, ths)]
+    try:
+        batch_primal_step(batch, [7, 0, 13])
+        assert [s.time for s in batch] == [7, 0, 13]
+        batch_primal_step(batch, [100, 50, 100])       # capped at the horizon
+        assert [s.time for s in batch] == [50, 50, 50]
+        batch_adjoint_step(batch, [5, 50, 20])
+        assert [s.adjoint_time for s in batch] == [45, 0, 30]
+        batch_adjoint_step(batch, 50)
+        got = [(s.objective(), s.gradient().cpu().numpy()) for s in batch]
+    finally:
+        for s in batch:
+            s.close()
+    for (J, g), P, th in zip(got, Ps, ths):
+        with Solver(P, th) as s:
+            s.run()
+            assert s.objective() == J
+            assert np.array_equal(s.gradient().cpu().numpy(), g)

@@ -75,3 +75,18 @@ def test_guards():
             s.mma_update(True, 1.5)
         s.mma_update(True, 0.2)
         assert s.time == 0                         # reset for the next solve
+
+
+def test_loop_with_the_frozen_schedule_against_oracle():
+    # the paper's schedule: per design iteration the primal, then as many
+    # ALBS iterations at its final state (Sec. 3.3)
+    P = _channel()
+    mask = inputs.design_mask(P)
+    th0 = np.where(mask, 0.5, 0.0).astype(np.float32)
+    prm = M.MMAParams(move=0.05)
+    th_o, hist_o, _ = Oracle(P, th0).mma(3, maximize=False, design=mask, prm=prm,
+                                         adjoint="frozen")
+    r = mma(P, th0, 3, maximize=False, move=0.05, design=mask.reshape(-1), adjoint="frozen")
+    for a, b in zip(r.history, hist_o):
+        assert abs(a - b) <= 1e-4 * abs(b), (a, b)
+    assert np.abs(r.theta - th_o.reshape(-1)).max() <= 1e-3

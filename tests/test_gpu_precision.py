@@ -1,9 +1,11 @@
-"""Reduced-precision population storage (BF16 / FP16 deviations from the rest
-weights, collision in FP32, FP64 objective and gradient accumulation).
+"""Reduced-precision population storage (BF16 / FP16 fluid deviations from
+the equilibrium at the reference velocity: the inlet velocity of an
+inlet/outlet channel, rest otherwise; scalars as values; collision in FP32,
+FP64 objective and gradient accumulation).
 
 Exactness where the arithmetic is the same: from a state that is already
 representable in the storage type, one primal step matches the FP64 oracle
-up to the final rounding of the output deviations to 16 bits, and one
+up to the final rounding of the stored output values to 16 bits, and one
 adjoint step (FP32 adjoint, 16-bit state) matches it to FP32 accuracy.
 
 Whole trajectories: the error against the FP64 oracle is measured and
@@ -64,6 +66,17 @@ def _random_state(o, seed):
     return F
 
 
+def _reference(o):
+    """(M, 1) values that 16-bit storage subtracts: the fluid equilibrium at
+    rho = 1 and the reference velocity (u_in along x for inlet/outlet
+    channels, rest otherwise), zero for the scalars."""
+    P, m = o.P, o.model
+    u = torch.tensor([[P.u_in if P.channel == "inlet_outlet" else 0.0], [0.0], [0.0]],
+                     dtype=torch.float64)
+    feq = m.feq(torch.ones(1, dtype=torch.float64), u).numpy()
+    return np.concatenate([feq, np.zeros((m.M - m.Q, 1))])
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_one_step_in_reduced_storage(name, prec):
@@ -86,10 +99,10 @@ def test_one_step_in_reduced_storage(name, prec):
         grad = _np(s.gradient())
     F0 = torch.tensor(f0).view(F.shape)
     ref = o.collide(F0).reshape(M, -1).numpy()
-    # output deviations are rounded once to the storage type
-    dev = np.abs(ref - np.concatenate([o.model.fl.w[:, None] * np.ones((o.model.Q, 1)),
-                                       np.zeros((M - o.model.Q, 1))])).max()
-    assert np.abs(post - ref).max() <= 1.01 * EPS[prec] * dev + 1e-6 * np.abs(ref).max()
+    # the stored values (fluid: f minus the reference equilibrium; scalars:
+    # g) are rounded once to the storage type
+    stored = np.abs(ref - _reference(o)).max()
+    assert np.abs(post - ref).max() <= 1.01 * EPS[prec] * stored + 1e-6 * np.abs(ref).max()
     gF, gth = o.adjoint_step(torch.tensor(lam, dtype=torch.float64).view(F.shape), F0)
     gF = gF.reshape(M, -1).numpy()
     gth = gth.numpy()

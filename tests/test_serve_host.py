@@ -33,16 +33,20 @@ class FakeSolver:
         FakeSolver.live -= 1
 
 
+def _ks(ss, k):
+    return list(k) if isinstance(k, (list, tuple)) else [k] * len(ss)
+
+
 def fake_primal(ss, k):
-    for s in ss:
-        s.time = min(s.P.nsteps, s.time + k)
+    for s, ki in zip(ss, _ks(ss, k)):
+        s.time = min(s.P.nsteps, s.time + ki)
 
 
 def fake_adjoint(ss, k):
-    for s in ss:
+    for s, ki in zip(ss, _ks(ss, k)):
         if s.adjoint_time < 0:
             s.adjoint_time = s.time
-        s.adjoint_time = max(0, s.adjoint_time - k)
+        s.adjoint_time = max(0, s.adjoint_time - ki)
 
 
 def _server(capacity, **kw):
@@ -124,3 +128,27 @@ def test_cancellation_releases_memory():
         else:
             assert r.error is None
     assert srv.committed == 0 and FakeSolver.live == 0
+
+
+def test_request_out_of_memory_in_a_batched_step_fails_alone():
+    # A batched step that runs out of device memory is retried one request at
+    # a time; the request whose pool cannot grow is retired with an error and
+    # its memory released, the others finish with their own results.
+    from paper_1501_04741_gb300.albm import AlbmError
+
+    def primal_oom(ss, k):
+        if any(s.P.nsteps == 77 for s in ss):
+            raise AlbmError(2, "cudaMalloc failed: out of memory")
+        fake_primal(ss, k)
+
+    reqs = _reqs(6, seed=3)
+    reqs[2] = Request(2, reqs[2].arrival, reqs[2].P.replace(nsteps=77), reqs[2].theta)
+    srv = Server(capacity_bytes=1e15, solver_factory=FakeSolver, primal_fn=primal_oom,
+                 adjoint_fn=fake_adjoint, mem_get_info=lambda: (0, 0))
+    FakeSolver.live = 0
+    srv.run(reqs)
+    assert reqs[2].error == "out of device memory"
+    assert srv.committed == 0 and FakeSolver.live == 0
+    for i, r in enumerate(reqs):
+        if i != 2:
+            assert r.error is None and r.J == float(np.asarray(r.theta, np.float64).sum())
