@@ -8,8 +8,19 @@ steps, then 10000 adjoint steps with level-1 checkpoints every 500 steps
 and recomputation of the states in between, accumulating dJ/dtheta in FP64.
 
 value = nodes * (primal steps + adjoint steps) / seconds / 1e6 (recomputed
-primal steps are work, not credit).  Inputs (550 MB of populations per
+primal steps are work, not credit), timed with CUDA events around whole
+solves; the per-kernel split (GB/s, roofline fraction) comes from one more
+solve with events around every launch.  Inputs (550 MB of populations per
 state) are larger than L2, so no flush is needed between steps.
+
+At N = 1 the same JSON line also carries the other workloads of the problem
+statement, measured on the same GPU after the headline: ``exchanger3d``
+(the 512x256x256 heat exchanger with FP32, BF16 and FP16 storage: solve
+MLUPS, kernel GB/s and dJ/dtheta against the FP32 path), ``serving``
+(Poisson-arriving requests at 1, 10 and 100 per second, 100 each, served
+with continuous batching against one-at-a-time FIFO service) and
+``batch64`` (64 instances through the batched autograd Function against
+one at a time); ``--no-extras`` leaves them out.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -62,7 +73,7 @@ def bytes_per_node(M: int, storage: int, kind: str) -> int:
 # the 256x128x128 lattice (traffic grows with the nodes); valid for the FP32
 # mixer kernels as captured: the forms without objective terms (primal
 # OBJ = 0, adjoint SRC = 0), which run 95 % of the steps.
-TRAFFIC_MIXER_FP32 = {"primal": 1.0268e9, "adjoint": 1.6741e9}
+TRAFFIC_MIXER_FP32 = {"primal": 1.0298e9, "adjoint": 1.6744e9}
 
 
 def workload(args) -> inputs.Problem:
@@ -155,25 +166,52 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 ORACLE_SAMPLE_DIMS = (96, 48, 48)
 ORACLE_SAMPLE_STEPS = 6
+ORACLE_SAMPLE_DIMS_1T = (48, 24, 24)
+ORACLE_SAMPLE_STEPS_1T = 4
+ORACLE_REPEATS = 5
 
 
-def oracle_sample(P: inputs.Problem):
+def oracle_sample(P: inputs.Problem, dims=ORACLE_SAMPLE_DIMS, steps=ORACLE_SAMPLE_STEPS):
     """Time the FP64 oracle on a bounded sample of the workload: the same
-    physics on a 96x48x48 sub-lattice, 6 primal then 6 adjoint steps."""
+    physics on a sub-lattice (96x48x48 by default), `steps` primal then
+    `steps` adjoint steps."""
     import torch
     from oracle.solver import Oracle
-    Ps = inputs.scaled(P, ORACLE_SAMPLE_DIMS, nsteps=ORACLE_SAMPLE_STEPS,
-                       obj_window=min(P.obj_window, ORACLE_SAMPLE_STEPS))
+    Ps = inputs.scaled(P, dims, nsteps=steps, obj_window=min(P.obj_window, steps))
     o = Oracle(Ps, inputs.theta_uniform(Ps, 0))
     t0 = time.perf_counter()
     _, traj = o.primal()
     o.adjoint(traj)
     dt = time.perf_counter() - t0
-    updates = o.n * ORACLE_SAMPLE_STEPS * 2
+    updates = o.n * steps * 2
     sample = (f"{Ps.lattice} {Ps.collision} + {Ps.nscalars} scalars on "
-              f"{'x'.join(map(str, ORACLE_SAMPLE_DIMS))}, {ORACLE_SAMPLE_STEPS} primal + "
-              f"{ORACLE_SAMPLE_STEPS} adjoint steps (FP64 oracle)")
+              f"{'x'.join(map(str, dims))}, {steps} primal + {steps} adjoint steps (FP64 oracle)")
     return updates / dt / 1e6, dt, torch.get_num_threads(), sample
+
+
+def cpu_baseline_record(P: inputs.Problem) -> dict:
+    """The oracle on the host cores: all threads torch uses (the reference
+    arm's sample and statistic: median of ORACLE_REPEATS runs after one
+    warm-up), and one thread on a smaller sample."""
+    import torch
+    oracle_sample(P)
+    runs = [oracle_sample(P) for _ in range(ORACLE_REPEATS)]
+    value = float(np.median([r[0] for r in runs]))
+    threads = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        oracle_sample(P, ORACLE_SAMPLE_DIMS_1T, ORACLE_SAMPLE_STEPS_1T)
+        one = [oracle_sample(P, ORACLE_SAMPLE_DIMS_1T, ORACLE_SAMPLE_STEPS_1T)
+               for _ in range(ORACLE_REPEATS)]
+    finally:
+        torch.set_num_threads(threads)
+    return {"value": value, "unit": UNIT, "cores": threads, "host_cpus": os.cpu_count(),
+            "kind": "oracle", "sample": runs[0][3],
+            "statistic": f"median of {ORACLE_REPEATS} runs after 1 warm-up",
+            "seconds_per_run": float(np.median([r[1] for r in runs])),
+            "single_thread": {"value": float(np.median([r[0] for r in one])), "unit": UNIT,
+                              "cores": 1, "sample": one[0][3],
+                              "statistic": f"median of {ORACLE_REPEATS} runs after 1 warm-up"}}
 
 
 def run_reference(args):
@@ -181,23 +219,22 @@ def run_reference(args):
     if rank != 0:
         return 0
     P = workload(args)
-    vals = []
     for _ in range(args.warmup):
         oracle_sample(P)
     t_all = time.perf_counter()
-    for _ in range(args.steps):
-        v, dt, cores, sample = oracle_sample(P)
-        vals.append(v)
+    runs = [oracle_sample(P) for _ in range(args.steps)]
     wall = time.perf_counter() - t_all
-    value = float(np.mean(vals))
+    value = float(np.median([r[0] for r in runs]))
+    cores, sample = runs[0][2], runs[0][3]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * wall / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(P, args),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                         "host_cpus": os.cpu_count(), "kind": "oracle", "sample": sample,
+                         "statistic": "median over the timed steps (one sample each)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -246,9 +283,9 @@ def run_ours(args):
     for _ in range(args.warmup):
         s.run()
     barrier()
+    # the timed region: whole solves, no per-launch instrumentation
     clocks = ClockSampler(local)
     clocks.start()
-    s.profile(True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
@@ -258,15 +295,18 @@ def run_ours(args):
         ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1)
-    prof = s.profile_read()
-    s.profile(False)
     clk = clocks.stop()
     J = s.objective()
     recompute = s.recompute_steps()
     updates_per_step = N * P.nsteps * 2
     ms_max, value = aggregate_ranks(ms, updates_per_step, args.steps, world)
 
-    # kernel-level numbers from the live event record
+    # kernel split: one more solve with CUDA events around every launch (the
+    # schedule of a solve after the warm-up is the same every time)
+    s.profile(True)
+    s.run()
+    prof = s.profile_read()
+    s.profile(False)
     n_p, ms_p = prof["primal"]
     n_r, ms_r = prof["recompute"]
     n_a, ms_a = prof["adjoint"]
@@ -282,27 +322,22 @@ def run_ours(args):
     ach = adj_gbs if dom == "adjoint" else prim_gbs
 
     # end to end through the C ABI with host buffers (pinned), copies inside
-    e2e = None
-    if rank == 0 or True:
-        th_host = torch.from_numpy(theta.reshape(-1)).pin_memory()
-        g_host = torch.empty(N, dtype=torch.float64).pin_memory()
-        s2 = s
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(max(1, args.e2e_steps)):
-            s2.set_theta(th_host.numpy())
-            s2.run()
-            s2.gradient(g_host.numpy())
-            s2.objective()
-        barrier()
-        dt = time.perf_counter() - t0
-        e2e = {"value": world * updates_per_step * max(1, args.e2e_steps) / dt / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": int(N * 4), "d2h_bytes_per_step": int(N * 8 + 16 * (P.nsteps + 1))}
-    launches = prof["launches"]
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        v, dt, cores, sample = oracle_sample(P)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    th_host = torch.from_numpy(theta.reshape(-1)).pin_memory()
+    g_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.e2e_steps)):
+        s.set_theta(th_host.numpy())
+        s.run()
+        s.gradient(g_host.numpy())
+        s.objective()
+    barrier()
+    dt = time.perf_counter() - t0
+    e2e = {"value": world * updates_per_step * max(1, args.e2e_steps) / dt / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(N * 4), "d2h_bytes_per_step": int(N * 8 + 16 * (P.nsteps + 1))}
+    s.close()
+    launches_per_solve = prof["launches"]
+    line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -319,28 +354,146 @@ def run_ours(args):
                                                                  not args.nsteps) else None),
                          "algorithmic_bytes": (bp if dom == "primal" else ba) * N},
             "kernels": {
+                "timing": "one solve after the timed region, CUDA events around every launch",
                 "primal": {"launches": n_p + n_r, "avg_ms": prim_ms, "GB_s": prim_gbs,
-                           "bytes_per_node": bp, "MLUPS": N / (prim_ms / 1e3) / 1e6},
+                           "frac": prim_gbs / peak, "bytes_per_node": bp,
+                           "MLUPS": N / (prim_ms / 1e3) / 1e6},
                 "adjoint": {"launches": n_a, "avg_ms": adj_ms, "GB_s": adj_gbs,
-                            "bytes_per_node": ba, "MLUPS": N / (adj_ms / 1e3) / 1e6},
+                            "frac": adj_gbs / peak, "bytes_per_node": ba,
+                            "MLUPS": N / (adj_ms / 1e3) / 1e6},
                 "share_adjoint": share_adj, "recompute_steps_per_solve": recompute},
             "J": J,
             "e2e": e2e,
-            "gpu_launches": int(launches),
+            "gpu_launches": int(launches_per_solve * args.steps),
             "clocks": clk,
-            "cpu_baseline": cpu,
+            "cpu_baseline": None,
         }
+        if world == 1 and not args.no_extras and args.workload == "mixer3d" and not args.nsteps:
+            # the other workloads of the problem statement, on the same GPU
+            line["exchanger3d"] = exchanger_precisions(args)
+            line["serving"] = serve_sweep(args)
+            line["batch64"] = batch64_record(args)
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_record(P)
         print(json.dumps(line), flush=True)
-    s.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
-def run_batch64(args):
-    """Config 4: 64 seeded D2Q9 / D3Q19 instances (sizes log-uniform, 1000-5000
-    steps) through the batched torch.autograd.Function, against the same
-    instances one at a time through the single-instance Function."""
+def exchanger_precisions(args) -> dict:
+    """The full 512x256x256 exchanger (1000 + 1000 steps) with FP32, BF16 and
+    FP16 population storage on one theta: solve MLUPS (one warm-up solve,
+    one timed solve without instrumentation), the kernels' GB/s from one
+    instrumented solve, and J and dJ/dtheta against the FP32 path."""
+    import torch
+    from paper_1501_04741_gb300.albm import Solver
+    P0 = inputs.exchanger3d()
+    th = torch.from_numpy(inputs.theta_grf(P0, 0).reshape(-1)).cuda()
+    stream = torch.cuda.Stream()
+    peak, _ = _peaks()
+    rows, ref = {}, None
+    for prec in ("fp32", "bf16", "fp16"):
+        P = P0.replace(precision=prec)
+        storage = 4 if prec == "fp32" else 2
+        with Solver(P, th, stream=stream) as s:
+            s.run()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.run()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            J = s.objective()
+            g = s.gradient().clone()
+            s.profile(True)
+            s.run()
+            prof = s.profile_read()
+            s.profile(False)
+            N, M = s.N, s.M
+        (n_p, ms_p), (n_r, ms_r), (n_a, ms_a) = prof["primal"], prof["recompute"], prof["adjoint"]
+        pm = (ms_p + ms_r) / max(n_p + n_r, 1)
+        am = ms_a / max(n_a, 1)
+        bp, ba = bytes_per_node(M, storage, "primal"), bytes_per_node(M, storage, "adjoint")
+        row = {"MLUPS": 2.0 * N * P.nsteps / (ms / 1e3) / 1e6, "solve_ms": ms, "J": J,
+               "primal": {"avg_ms": pm, "bytes_per_node": bp, "GB_s": bp * N / pm / 1e6,
+                          "frac": bp * N / pm / 1e6 / peak},
+               "adjoint": {"avg_ms": am, "bytes_per_node": ba, "GB_s": ba * N / am / 1e6,
+                           "frac": ba * N / am / 1e6 / peak}}
+        if ref is None:
+            ref = (J, g)
+        else:
+            row["J_rel_err_vs_fp32"] = abs(J - ref[0]) / abs(ref[0])
+            row["dJdtheta_rel_err_vs_fp32"] = float((g - ref[1]).abs().max() / ref[1].abs().max())
+        rows[prec] = row
+        del g
+    return {"dims": list(P0.dims), "steps": P0.nsteps, "objective": P0.objective,
+            "theta": "Gaussian random field (sigma 4) on the middle 3/7", "rows": rows}
+
+
+def serve_sweep(args) -> dict:
+    """Config 5 served with continuous batching at several arrival rates,
+    against one-at-a-time plain FP32 FIFO service of the same requests.
+
+    The same seeded requests serve every rate (arrival times scale as 1 /
+    rate).  The one-at-a-time baseline solves each request alone once and
+    times it (handle creation, solve, J and dJ/dtheta to the host); its FIFO
+    latencies at each rate follow from those service times and the arrival
+    times (start = max(arrival, previous finish)), which is what a real-time
+    one-at-a-time server would see, without waiting out the idle gaps."""
+    import torch
+    from paper_1501_04741_gb300.albm import Solver
+    from paper_1501_04741_gb300.serve import Request, Server
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    count = args.serve_count
+    spec1 = inputs.serving_requests(count, rate=1.0, seed=0, node_range=(1e4, args.max_nodes))
+    # one-at-a-time service times (plain FP32 handles, one after the other)
+    stream = torch.cuda.Stream()
+    svc, J_alone, g_alone = [], [], []
+    for _, P, th in spec1:
+        t0 = time.perf_counter()
+        with Solver(P, th, stream=stream) as s:
+            s.run()
+            J_alone.append(s.objective())
+            g_alone.append(s.gradient().cpu().numpy())
+        svc.append(time.perf_counter() - t0)
+    updates = float(sum(2.0 * P.n_nodes * P.nsteps for _, P, _ in spec1))
+    rows = []
+    for rate in rates:
+        arrivals = [t / rate for t, _, _ in spec1]
+        done, fin = [], 0.0
+        for a, sv in zip(arrivals, svc):
+            fin = max(a, fin) + sv
+            done.append(fin)
+        lat_seq = [d - a for d, a in zip(done, arrivals)]
+        reqs = [Request(i, a, P, th) for i, (a, (_, P, th)) in enumerate(zip(arrivals, spec1))]
+        srv = Server(steps_per_tick=args.tick, keep_gradients=True)
+        st = srv.run(reqs)
+        torch.cuda.synchronize()
+        ok = all(r.error is None for r in reqs)
+        same = ok and all(r.J == j and np.array_equal(r.grad, g)
+                          for r, j, g in zip(reqs, J_alone, g_alone))
+        for r in reqs:
+            r.grad = None
+        rows.append({"rate_per_s": rate, "requests": len(reqs),
+                     "served": {"p50_s": st.p50, "p99_s": st.p99, "MLUPS": st.mlups,
+                                "makespan_s": st.makespan, "max_resident": st.max_resident},
+                     "one_at_a_time": {"p50_s": float(np.percentile(lat_seq, 50)),
+                                       "p99_s": float(np.percentile(lat_seq, 99)),
+                                       "MLUPS": updates / max(done[-1], 1e-9) / 1e6,
+                                       "makespan_s": done[-1]},
+                     "results_identical_to_alone": bool(same)})
+    return {"requests_per_rate": count, "node_range": [1e4, args.max_nodes],
+            "steps_range": [500, 5000], "lattices": "D2Q9 / D3Q19 channels at 50/50",
+            "service_s_total": float(sum(svc)), "rows": rows}
+
+
+def batch64_record(args) -> dict:
+    """Config 4: 64 seeded D2Q9 / D3Q19 instances (sizes log-uniform,
+    1000-5000 steps) through the batched torch.autograd.Function, against
+    the same instances one at a time through the single-instance Function."""
     import torch
     from paper_1501_04741_gb300.albm import Solver
     from paper_1501_04741_gb300.autograd import albm_objective, albm_objectives
@@ -372,52 +525,34 @@ def run_batch64(args):
     t_seq = time.perf_counter() - t0
     finite = all(bool(torch.isfinite(t.grad).all()) for t in thetas)
     same = all(torch.equal(a, t.grad) for a, t in zip(g_batch, thetas))
-    gdiff = max(float((a.double() - t.grad.double()).abs().max() / t.grad.double().abs().max().clamp_min(1e-300))
-                for a, t in zip(g_batch, thetas))
     for s in solvers:
         s.close()
-    print(json.dumps({
-        "metric": "batched autograd primal+adjoint MLUPS", "workload": "batch64",
-        "value": updates / t_batch / 1e6, "unit": UNIT, "higher_is_better": True,
-        "instances": len(batch), "nodes_total": sum(P.n_nodes for P, _ in batch),
-        "d2q9": sum(P.lattice == "D2Q9" for P, _ in batch),
-        "batched_s": t_batch, "one_at_a_time_s": t_seq,
-        "one_at_a_time_MLUPS": updates / t_seq / 1e6,
-        "gradients_identical": bool(same), "gradient_max_rel_diff": gdiff,
-        "gradients_finite": finite,
-        "size_scale": args.size_scale}), flush=True)
+    return {"instances": len(batch), "nodes_total": sum(P.n_nodes for P, _ in batch),
+            "d2q9": sum(P.lattice == "D2Q9" for P, _ in batch), "size_scale": args.size_scale,
+            "batched_MLUPS": updates / t_batch / 1e6, "batched_s": t_batch,
+            "one_at_a_time_MLUPS": updates / t_seq / 1e6, "one_at_a_time_s": t_seq,
+            "gradients_identical": bool(same), "gradients_finite": finite}
+
+
+def run_batch64(args):
+    rec = batch64_record(args)
+    print(json.dumps({"metric": "batched autograd primal+adjoint MLUPS", "workload": "batch64",
+                      "value": rec["batched_MLUPS"], "unit": UNIT, "higher_is_better": True,
+                      **rec}), flush=True)
     return 0
 
 
 def run_serve(args):
-    """Config 5: Poisson-arriving sensitivity requests (D2Q9 or D3Q19 at
-    50/50, 1e4..3e7 nodes log-uniform, 500..5000 steps), served with
-    continuous batching, against one-at-a-time plain FP32 solves."""
-    import torch
-    from paper_1501_04741_gb300.serve import Request, Server, run_sequential
-    rates = [float(r) for r in args.rates.split(",")]
-    rows = []
-    for rate in rates:
-        spec = inputs.serving_requests(args.count or 12, rate=rate, seed=int(rate * 10),
-                                       node_range=(1e4, args.max_nodes))
-        reqs = [Request(i, t, P, th) for i, (t, P, th) in enumerate(spec)]
-        srv = Server(steps_per_tick=args.tick, keep_gradients=False)
-        st = srv.run(reqs)
-        torch.cuda.synchronize()
-        seq = [Request(i, t, P, th) for i, (t, P, th) in enumerate(spec)]
-        sq = run_sequential(seq, keep_gradients=False)
-        same = all(a.J == b.J for a, b in zip(reqs, seq))
-        jdiff = max(abs(a.J - b.J) / max(abs(b.J), 1e-300) for a, b in zip(reqs, seq))
-        row = {"rate_per_s": rate, "requests": len(reqs),
-               "batched": {"p50_s": st.p50, "p99_s": st.p99, "MLUPS": st.mlups,
-                           "makespan_s": st.makespan, "max_resident": st.max_resident},
-               "one_at_a_time": {"p50_s": sq.p50, "p99_s": sq.p99, "MLUPS": sq.mlups,
-                                 "makespan_s": sq.makespan},
-               "J_identical": bool(same), "J_max_rel_diff": jdiff}
-        rows.append(row)
-        print(json.dumps(row), flush=True)
+    rec = serve_sweep(args)
     print(json.dumps({"metric": "served p50/p99 vs one-at-a-time FP32", "workload": "serve",
-                      "max_nodes": args.max_nodes, "rows": rows}), flush=True)
+                      **rec}), flush=True)
+    return 0
+
+
+def run_precision(args):
+    rec = exchanger_precisions(args)
+    print(json.dumps({"metric": "exchanger solve MLUPS and dJ/dtheta error by storage",
+                      "workload": "precision", **rec}), flush=True)
     return 0
 
 
@@ -640,7 +775,8 @@ def run_profile_case(args):
     # 6 steps with a 2-step objective window: primal launches 1-4 and
     # adjoint launches 3-6 are the no-objective kernels that dominate a long
     # horizon, the others carry the objective terms
-    P = inputs.scaled(inputs.mixer3d(), (256, 128, 64), nsteps=6, obj_window=2, ckpt_every=1,
+    base = inputs.exchanger3d() if args.workload == "exchanger3d" else inputs.mixer3d()
+    P = inputs.scaled(base, (256, 128, 64), nsteps=6, obj_window=2, ckpt_every=1,
                       precision=args.precision, kernel=args.kernel)
     th = torch.from_numpy(inputs.theta_uniform(P, 0).reshape(-1)).cuda()
     with Solver(P, th) as s:
@@ -648,7 +784,8 @@ def run_profile_case(args):
         s.adjoint_step(P.nsteps)
         J = s.objective()
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": "mixer3d 256x128x64", "precision": args.precision, "J": J}))
+    print(json.dumps({"profile_case": f"{args.workload} 256x128x64", "precision": args.precision,
+                      "J": J}))
     return 0
 
 
@@ -667,18 +804,22 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="mixer3d",
                     choices=["mixer3d", "exchanger3d", "batch64", "serve", "oneshot", "meshes",
-                             "paper", "mma"])
-    ap.add_argument("--count", type=int, default=0, help="instances (batch64) or requests (serve)")
+                             "paper", "mma", "precision"])
+    ap.add_argument("--count", type=int, default=0, help="batch64: instances (default 64)")
     ap.add_argument("--size-scale", type=float, default=1.0, help="batch64: linear size factor")
-    ap.add_argument("--rates", default="2,20,200", help="serve: arrival rates per second")
-    ap.add_argument("--max-nodes", type=float, default=3e7, help="serve: largest request")
+    ap.add_argument("--serve-rates", default="1,10,100", help="serve: arrival rates per second")
+    ap.add_argument("--serve-count", type=int, default=100, help="serve: requests per rate")
+    ap.add_argument("--max-nodes", type=float, default=1e6, help="serve: largest request")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="mixer3d: skip the exchanger precision, serving and batch64 records")
     ap.add_argument("--tick", type=int, default=200, help="serve: most steps per request per tick")
     ap.add_argument("--oneshot-iters", type=int, default=200,
                     help="oneshot: one-shot iterations per timed step")
     ap.add_argument("--profile-case", action="store_true",
-                    help="run the small ncu case instead: mixer3d physics on 256x128x64, "
-                         "6 primal + 6 adjoint steps, objective over the last 2 "
-                         "(277 MB per state, > L2)")
+                    help="run the small ncu case instead: the mixer3d (or, with --workload "
+                         "exchanger3d, the exchanger) physics on 256x128x64, 6 primal + 6 "
+                         "adjoint steps, objective over the last 2 (277 MB per FP32 mixer "
+                         "state, > L2)")
     args = ap.parse_args(argv)
     if args.profile_case:
         return run_profile_case(args)
@@ -694,6 +835,8 @@ def main(argv=None):
         return run_paper(args)
     if args.workload == "mma":
         return run_mma(args)
+    if args.workload == "precision":
+        return run_precision(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
