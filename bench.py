@@ -712,9 +712,23 @@ def run_paper(args):
                      "T_mean": Tm, "T_sd": Ts, "T_paper": ref["T"],
                      "primal_MLUPS": P.n_nodes * P.nsteps / dt / 1e6})
         print(json.dumps(rows[-1]), flush=True)
-    print(json.dumps({"metric": "paper empty channels vs Tab. tab:results", "workload": "paper",
-                      "unit": UNIT, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-                      "rows": rows}), flush=True)
+    # the fin study of Sec. 4.2 on the exchanger (row "Fins")
+    from tests.test_gpu_paper_tables import _golden_fins, run_fins
+    P = inputs.paper_exchanger_empty()
+    fins = []
+    for n, w in inputs.fin_sweep(P):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, (um, us, Tm, Ts) = run_fins(P, n, w)
+        dt = time.perf_counter() - t0
+        fins.append({"fins": n, "width": w, "J": J, "u_mean": um, "u_sd": us, "T_mean": Tm,
+                     "T_sd": Ts, "primal_MLUPS": P.n_nodes * P.nsteps / dt / 1e6})
+    best = max(fins, key=lambda r: r["J"])
+    fref = _golden_fins()
+    print(json.dumps({"metric": "paper empty channels and fin study vs Tab. tab:results",
+                      "workload": "paper", "unit": UNIT, "n_gpus": 1, "dtype": "f32",
+                      "data": "synthetic", "rows": rows, "fins": fins,
+                      "fins_best": best, "fins_paper": fref}), flush=True)
     return 0
 
 

@@ -73,7 +73,7 @@ typedef enum {
 enum {
   LBM_NODE_FLUID = 0,  /* FMRT/BGK with Exact-Difference forcing and porosity */
   LBM_NODE_WALL = 1,   /* full-way bounce-back of every lattice               */
-  LBM_NODE_INLET = 2,  /* Zou-He velocity inlet on the x = 0 face             */
+  LBM_NODE_INLET = 2,  /* Zou-He inlet on the x = 0 face (velocity/pressure) */
   LBM_NODE_OUTLET = 3, /* Zou-He pressure outlet on the x = Lx-1 face         */
   LBM_NODE_HOT = 4     /* fluid bounce-back, scalars at equilibrium T_hot     */
 };
@@ -120,6 +120,13 @@ typedef struct {
                            fixed-point ALBS at the held state f-hat = f^N
                            (Sec. 2.2, Eqs. adjoint:iteration/adjoint:operator
                            at the stationary state), needs obj_window 0      */
+  int inlet_kind;       /* inlet_outlet channels: 0 velocity inlet u_x = u_in;
+                           1 pressure inlet (Sec. 4): rho = rho_out + 3 dp
+                           (the pressure drop dp over the outlet, p = rho/3),
+                           with the inlet velocity capped at u_in (a node
+                           whose pressure condition would exceed the cap is
+                           a velocity inlet at the cap)                      */
+  double dp;            /* pressure drop of a pressure inlet                 */
 } lbm_params;
 
 /* Create a solver.  Defines the lattice, node types, collision (Sec. 3,
@@ -225,6 +232,17 @@ lbm_status lbm_get_flags(lbm_handle h, uint8_t* dst);
 /* Count non-finite values in the current state (0 = healthy); synchronises.
  * Returns LBM_ERR_NONFINITE when the count is positive. */
 lbm_status lbm_check_finite(lbm_handle h, long long* count_host);
+
+/* Bound of the tile-staged kernels' (lbm_params.kernel 2) waits for the
+ * shared-memory copies of a stage: polls >= 0 polls (0: give up at the first
+ * wait), polls < 0: the default of 2^22 polls.  A block that gives up records
+ * the failure, waits (with the default bound) for every copy it still has
+ * in flight and returns; the next synchronising call (lbm_objective,
+ * lbm_gradient to host memory, lbm_check_finite, ...) returns
+ * LBM_ERR_TIMEOUT, the state of that step is not valid and lbm_reset starts
+ * over.  Lets a test drive the timeout path without a fault.  Errors:
+ * LBM_ERR_ARG. */
+lbm_status lbm_set_wait_polls(lbm_handle h, long long polls);
 
 /* Move the handle to another CUDA stream (NULL = legacy default).  Work
  * already queued for the handle on its old stream is ordered before any

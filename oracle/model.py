@@ -16,8 +16,11 @@ code  name       W^x
 0     FLUID      FMRT (Sec. 3.1) or BGK (Eq. SRT) with Exact-Difference
                  forcing; Darcy porosity u_post = G(theta) u_pre + g (Sec. 3.2)
 1     WALL       full-way bounce-back W_j = f_opp(j) for every lattice
-2     INLET      Zou-He velocity inlet on the x = 0 face, then the FLUID W;
-                 scalars set to equilibrium at the inlet value
+2     INLET      Zou-He inlet on the x = 0 face, then the FLUID W; velocity
+                 inlet (u = u_in) or pressure inlet (rho = rho_out + 3 dp)
+                 whose velocity is capped at u_in (above the cap the node is
+                 a velocity inlet at the cap, Sec. 4); scalars set to
+                 equilibrium at the inlet value with the node's velocity
 3     OUTLET     Zou-He pressure outlet on the x = Lx-1 face, then the FLUID
                  W; the unknown scalar populations are set to equilibrium at
                  the node's own scalar value, solved from the known ones
@@ -160,6 +163,21 @@ class Model:
             rows[i] = val
         return torch.stack(rows), rho, u
 
+    def inlet(self, f):
+        """Zou-He reconstruction at the x = 0 face.  Velocity inlet: u_x =
+        u_in.  Pressure inlet (Sec. 4: the inlet pressure is the pressure
+        drop over the outlet's reference, p = cs2 rho): rho = rho_out + dp /
+        cs2, giving u_x = 1 - (s0 + 2 s_out) / rho; where that exceeds the
+        limit u_in the node is a velocity inlet at u_in instead."""
+        P = self.P
+        if P.inlet == "velocity":
+            return self.zou_he(f, +1, u_n=P.u_in)[0]
+        if P.inlet != "pressure":
+            raise ValueError(P.inlet)
+        f_p, _, u_p = self.zou_he(f, +1, rho=P.rho_out + P.dp / self.fl.cs2)
+        f_c, _, _ = self.zou_he(f, +1, u_n=P.u_in)
+        return torch.where(u_p[0] > P.u_in, f_c, f_p)
+
     def scalar_outlet(self, g, v):
         """Outlet scalar: unknown populations (e_x < 0) at equilibrium with the
         node's own value T*, solved from the known ones:
@@ -203,7 +221,7 @@ class Model:
         is_out = (flags == OUTLET)
         fr = f
         if P.channel == "inlet_outlet":
-            f_in, _, _ = self.zou_he(f, +1, u_n=P.u_in)
+            f_in = self.inlet(f)
             f_out, _, _ = self.zou_he(f, -1, rho=P.rho_out)
             fr = torch.where(is_in, f_in, torch.where(is_out, f_out, f))
         rho = fr.sum(0)
@@ -245,8 +263,8 @@ class Model:
             omT = 1.0 / (0.5 + self.alpha(theta) / self.sl.cs2)
             Wg = gr + omT * (self.geq(T, v) - gr)
             if P.channel == "inlet_outlet":
-                u_in = torch.tensor([P.u_in, 0.0, 0.0], dtype=DT)[:, None]
-                g_in = self.geq(self.inlet_scalar(s, y), u_in.expand(3, g.shape[1]))
+                # equilibrium at the inlet value and the node's inlet velocity
+                g_in = self.geq(self.inlet_scalar(s, y), u)
                 Wg = torch.where(flags == INLET, g_in, Wg)
             Wg = torch.where(flags == WALL, g[self.sl.opp], Wg)
             if P.hot:

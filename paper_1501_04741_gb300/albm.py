@@ -28,6 +28,7 @@ OBJECTIVE = {"none": 0, "dissipation": 1, "variance": 2, "heatflux_dp": 3, "mixf
 SCALAR_INLET = {"zero": 0, "halves": 1, "signed": 2}
 KERNEL = {"auto": 0, "plain": 1, "tiles": 2, "async": 3}
 ADJOINT_MODE = {"unsteady": 0, "frozen": 1}
+INLET = {"velocity": 0, "pressure": 1}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
           4: "LBM_ERR_NONFINITE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 
@@ -43,7 +44,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_theta", "lbm_
            "lbm_threshold_apply", "lbm_get_theta", "lbm_mma_reset", "lbm_mma_update",
            "lbm_mma_update_with", "lbm_state_objective_noalloc",
            "lbm_noalloc_last_error", "lbm_set_stream", "lbm_batch_primal_steps",
-           "lbm_batch_adjoint_steps"]
+           "lbm_batch_adjoint_steps", "lbm_set_wait_polls"]
 
 
 class LbmParams(C.Structure):
@@ -57,6 +58,7 @@ class LbmParams(C.Structure):
         ("porosity_q", C.c_double), ("objective", C.c_int), ("obj_window", C.c_int),
         ("nsteps", C.c_int), ("precision", C.c_int), ("ckpt_every", C.c_int),
         ("mem_budget", C.c_double), ("kernel", C.c_int), ("adjoint_mode", C.c_int),
+        ("inlet_kind", C.c_int), ("dp", C.c_double),
     ]
 
 
@@ -118,6 +120,7 @@ def lib():
         L.lbm_mma_update.argtypes = [vp, i, d]
         L.lbm_mma_update_with.argtypes = [vp, vp, i, d]
         L.lbm_set_stream.argtypes = [vp, vp]
+        L.lbm_set_wait_polls.argtypes = [vp, C.c_longlong]
         L.lbm_state_objective_noalloc.argtypes = [C.POINTER(LbmParams), vp, vp, vp, vp,
                                                   C.POINTER(d)]
         L.lbm_noalloc_last_error.argtypes = []
@@ -157,6 +160,8 @@ def make_params(P: Problem, mem_budget: float = 0.0) -> LbmParams:
     p.mem_budget = float(mem_budget)
     p.kernel = KERNEL[P.kernel]
     p.adjoint_mode = ADJOINT_MODE[P.adjoint_mode]
+    p.inlet_kind = INLET[P.inlet]
+    p.dp = float(P.dp)
     return p
 
 
@@ -329,6 +334,10 @@ class Solver:
         self._check(self._L.lbm_get_adjoint(self._h, _ptr(out)))
         self._sync_out()
         return out
+
+    def set_wait_polls(self, polls: int):
+        """Bound of the tile-staged kernels' waits (< 0: the default)."""
+        self._check(self._L.lbm_set_wait_polls(self._h, int(polls)))
 
     def set_stream(self, stream):
         """Move the handle to ``stream`` (a torch.cuda.Stream); its queued work

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <set>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -55,13 +56,16 @@ struct lbm_ctx {
   int lam_cur = 0;
   size_t state_bytes = 0;
   size_t state_stride = 0;          // state_bytes rounded up to 256
-  int slab_states = 1;              // states per allocation (small states share slabs)
-  std::vector<void*> slabs;         // allocations holding several states
+  int slab_states = 1;              // most states per allocation
+  std::vector<void*> slabs;         // the allocations holding the states
   char* slab_next = nullptr;
   int slab_left = 0;
-  std::vector<char> buf_in_slab;
   std::vector<void*> bufs;
-  std::vector<int> buf_time;        // time held by each buffer, -1 = free
+  std::vector<int> buf_time;        // per buffer: time held, -1 free, -2 reserved
+  std::vector<int> time_buf;        // per time 0..nsteps: the buffer holding it, or -1
+  std::vector<int> free_bufs;       // buffers that became free (stack)
+  std::set<int> held;               // times held
+  std::set<int> evictable;          // held times that are not level-1 checkpoints
   int max_bufs = 3;
   int ckpt = 1;                     // level-1 stride
   int t = 0;                        // primal time
@@ -156,46 +160,82 @@ bool is_device_ptr(const void* p) {
 // ---------------------------------------------------------------------------
 // buffer pool
 // ---------------------------------------------------------------------------
+// Every change of a buffer's label goes through set_time, which keeps the
+// time -> buffer index, the sets of held and evictable times and the stack
+// of free buffers in step, so that every lookup of a step is O(1) or
+// O(log n) in the number of held states (a linear scan per step would make
+// a long horizon quadratic on the host).
+static void set_time(lbm_ctx* h, int b, int t) {
+  const int old = h->buf_time[b];
+  if (old == t) return;
+  if (old >= 0) {
+    h->time_buf[old] = -1;
+    h->held.erase(old);
+    h->evictable.erase(old);
+  }
+  h->buf_time[b] = t;
+  if (t >= 0) {
+    h->time_buf[t] = b;
+    h->held.insert(t);
+    if (t % h->ckpt != 0) h->evictable.insert(t);
+  } else if (t == -1) {
+    h->free_bufs.push_back(b);
+  }
+}
+
+static void reset_pool(lbm_ctx* h) {
+  for (size_t b = 0; b < h->bufs.size(); ++b) set_time(h, (int)b, -1);
+}
+
 static int find_buf(lbm_ctx* h, int t) {
-  for (size_t i = 0; i < h->bufs.size(); ++i)
-    if (h->buf_time[i] == t) return (int)i;
+  return (t >= 0 && t < (int)h->time_buf.size()) ? h->time_buf[t] : -1;
+}
+
+static int n_kept(lbm_ctx* h) { return (int)h->held.size(); }
+
+// a free buffer, reserved (-2) for the caller, or -1
+static int pop_free(lbm_ctx* h) {
+  while (!h->free_bufs.empty()) {
+    const int b = h->free_bufs.back();
+    h->free_bufs.pop_back();
+    if (h->buf_time[b] == -1) {
+      set_time(h, b, -2);
+      return b;
+    }
+  }
   return -1;
 }
 
-static int n_kept(lbm_ctx* h) {
-  int n = 0;
-  for (int v : h->buf_time) n += v >= 0;
-  return n;
-}
-
+// A buffer reserved (-2) for the caller, who labels it with set_time.
 static lbm_status acquire(lbm_ctx* h, int* out) {
-  for (size_t i = 0; i < h->bufs.size(); ++i)
-    if (h->buf_time[i] == -1) {
-      *out = (int)i;
-      return LBM_OK;
-    }
+  const int fb = pop_free(h);
+  if (fb >= 0) {
+    *out = fb;
+    return LBM_OK;
+  }
   if ((int)h->bufs.size() >= h->max_bufs)
     FAIL(h, LBM_ERR_OOM, "state pool exhausted (%d buffers of %zu bytes)", h->max_bufs,
          h->state_bytes);
-  void* p = nullptr;
-  if (h->slab_states > 1) {
-    if (h->slab_left == 0) {
-      const int n = std::min(h->slab_states, h->max_bufs - (int)h->bufs.size());
-      void* slab = nullptr;
-      CK(h, cudaMalloc(&slab, (size_t)n * h->state_stride));
-      h->slabs.push_back(slab);
-      h->slab_next = (char*)slab;
-      h->slab_left = n;
-    }
-    p = h->slab_next;
-    h->slab_next += h->state_stride;
-    h->slab_left--;
-  } else {
-    CK(h, cudaMalloc(&p, h->state_bytes));
+  if (h->slab_left == 0) {
+    // the pool grows by slabs of several states: as many as it holds
+    // already (at least 4), at most about 1 GiB and never past the budget,
+    // so that a long trajectory costs a few dozen allocations, and freeing
+    // the pool (cudaFree synchronises the device) a few dozen frees
+    const int held = (int)h->bufs.size();
+    int n = std::max(4, held);
+    n = std::min(n, h->slab_states);
+    n = std::min(n, h->max_bufs - held);
+    void* slab = nullptr;
+    CK(h, cudaMalloc(&slab, (size_t)n * h->state_stride));
+    h->slabs.push_back(slab);
+    h->slab_next = (char*)slab;
+    h->slab_left = n;
   }
+  void* p = h->slab_next;
+  h->slab_next += h->state_stride;
+  h->slab_left--;
   h->bufs.push_back(p);
-  h->buf_in_slab.push_back(h->slab_states > 1 ? 1 : 0);
-  h->buf_time.push_back(-1);
+  h->buf_time.push_back(-2);
   *out = (int)h->bufs.size() - 1;
   return LBM_OK;
 }
@@ -205,24 +245,19 @@ static lbm_status acquire(lbm_ctx* h, int* out) {
 // checkpoint nor `keep`.  The forward pass thus leaves the most recent states
 // in the pool, which the adjoint needs first, instead of recomputing them.
 static lbm_status acquire_evict(lbm_ctx* h, int keep, int* out) {
-  for (size_t i = 0; i < h->bufs.size(); ++i)
-    if (h->buf_time[i] == -1) {
-      *out = (int)i;
-      return LBM_OK;
-    }
-  if ((int)h->bufs.size() < h->max_bufs) return acquire(h, out);
-  int best = -1, best_t = 0;
-  for (size_t i = 0; i < h->bufs.size(); ++i) {
-    const int t = h->buf_time[i];
-    if (t >= 0 && t != keep && t % h->ckpt != 0 && (best < 0 || t < best_t)) {
-      best = (int)i;
-      best_t = t;
-    }
+  const int fb = pop_free(h);
+  if (fb >= 0) {
+    *out = fb;
+    return LBM_OK;
   }
-  if (best < 0)
+  if ((int)h->bufs.size() < h->max_bufs) return acquire(h, out);
+  auto it = h->evictable.begin();
+  if (it != h->evictable.end() && *it == keep) ++it;
+  if (it == h->evictable.end())
     FAIL(h, LBM_ERR_OOM, "state pool exhausted by checkpoints (%d buffers of %zu bytes)",
          h->max_bufs, h->state_bytes);
-  h->buf_time[best] = -1;
+  const int best = h->time_buf[*it];
+  set_time(h, best, -2);
   *out = best;
   return LBM_OK;
 }
@@ -366,6 +401,26 @@ __global__ void __launch_bounds__(256) fluid_mask_kernel(long long N, const uint
 }
 }  // namespace albm
 
+// the runtime's own kernels, loaded once per device (see Launch::preload)
+static cudaError_t preload_runtime_kernels() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load() & bit) return cudaSuccess;
+  cudaFuncAttributes fa;
+  const void* ks[] = {(const void*)albm::fold_partials_kernel, (const void*)albm::penalty_kernel,
+                      (const void*)albm::threshold_kernel, (const void*)albm::mma_update_kernel,
+                      (const void*)albm::fluid_mask_kernel};
+  for (const void* k : ks) {
+    e = cudaFuncGetAttributes(&fa, k);
+    if (e != cudaSuccess) return e;
+  }
+  done.fetch_or(bit);
+  return cudaSuccess;
+}
+
 // after a synchronisation: report an expired bounded wait of a staged kernel
 static lbm_status check_timeout(lbm_ctx* h) {
   if (!h->d_err) return LBM_OK;
@@ -421,13 +476,10 @@ static lbm_status record_final_objective(lbm_ctx* h) {
 // make f^n available in the pool (recompute from the latest kept state < n)
 static lbm_status ensure_state(lbm_ctx* h, int n) {
   if (find_buf(h, n) >= 0) return LBM_OK;
-  int c = -1, cb = -1;
-  for (size_t i = 0; i < h->bufs.size(); ++i)
-    if (h->buf_time[i] >= 0 && h->buf_time[i] < n && h->buf_time[i] > c) {
-      c = h->buf_time[i];
-      cb = (int)i;
-    }
-  if (cb < 0) FAIL(h, LBM_ERR_STATE, "no kept state before time %d", n);
+  auto it = h->held.lower_bound(n);
+  if (it == h->held.begin()) FAIL(h, LBM_ERR_STATE, "no kept state before time %d", n);
+  --it;
+  const int c = *it, cb = h->time_buf[c];
   const int L = n - c;
   const int free_now = h->max_bufs - n_kept(h);
   // states to keep on this pass
@@ -451,7 +503,7 @@ static lbm_status ensure_state(lbm_ctx* h, int n) {
   // on failure the scratch buffers go back to the pool (kept states stay valid)
   auto release = [&](lbm_status s) {
     for (int j = 0; j < 2; ++j)
-      if (scratch[j] >= 0 && h->buf_time[scratch[j]] == -2) h->buf_time[scratch[j]] = -1;
+      if (scratch[j] >= 0 && h->buf_time[scratch[j]] == -2) set_time(h, scratch[j], -1);
     return s;
   };
   for (int k = 1; k <= L; ++k) {
@@ -465,9 +517,8 @@ static lbm_status ensure_state(lbm_ctx* h, int n) {
       for (int j = 0; j < 2; ++j)
         if (scratch[j] >= 0 && scratch[j] != cur) pick = scratch[j];
       if (pick < 0) {
-        lbm_status s = acquire(h, &pick);
+        lbm_status s = acquire(h, &pick);   // reserved (-2) as scratch
         if (s) return release(s);
-        h->buf_time[pick] = -2;  // reserved as scratch
         if (scratch[0] < 0) scratch[0] = pick; else scratch[1] = pick;
       }
       dst = pick;
@@ -475,12 +526,11 @@ static lbm_status ensure_state(lbm_ctx* h, int n) {
     lbm_status s = launch_primal(h, cur, dst, c + k - 1, false, K_RECOMPUTE);
     if (s) return release(s);
     h->recompute_steps++;
-    if (keep[k]) h->buf_time[dst] = c + k;
-    else h->buf_time[dst] = -2;
+    set_time(h, dst, keep[k] ? c + k : -2);
     cur = dst;
   }
   for (int j = 0; j < 2; ++j)
-    if (scratch[j] >= 0 && h->buf_time[scratch[j]] == -2) h->buf_time[scratch[j]] = -1;
+    if (scratch[j] >= 0 && h->buf_time[scratch[j]] == -2) set_time(h, scratch[j], -1);
   return LBM_OK;
 }
 
@@ -508,7 +558,7 @@ static lbm_status launch_adjoint(lbm_ctx* h, int n, int has_next) {
 
 static lbm_status do_reset(lbm_ctx* h) {
   h->oneshot = false;
-  for (auto& t : h->buf_time) t = -1;
+  reset_pool(h);
   int b;
   lbm_status s = acquire(h, &b);
   if (s) return s;
@@ -520,7 +570,7 @@ static lbm_status do_reset(lbm_ctx* h) {
     CK(h, h->ks.rest(h->kp, a, h->stream));
     h->launches_other++;
   }
-  h->buf_time[b] = 0;
+  set_time(h, b, 0);
   h->t = 0;
   h->t_adj = -1;
   h->recompute_steps = 0;
@@ -568,6 +618,9 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   else if (p.porosity == LBM_POR_POWER && p.porosity_q < 1.0) st = bad("power porosity needs q >= 1");
   else if (p.inlet_outlet && (p.nx < 3 || !(p.u_in < 1.0) || !(p.rho_out > 0.0)))
     st = bad("inlet_outlet needs nx >= 3, u_in < 1 and rho_out > 0");
+  else if (p.inlet_kind < 0 || p.inlet_kind > 1) st = bad("inlet_kind must be 0 or 1");
+  else if (p.inlet_kind == 1 && !(p.rho_out + 3.0 * p.dp > 0.0))
+    st = bad("a pressure inlet needs rho_out + 3 dp > 0");
   else if (p.adjoint_mode < 0 || p.adjoint_mode > 1) st = bad("adjoint_mode must be 0 or 1");
   else if (p.adjoint_mode == 1 && p.obj_window != 0)
     st = bad("the fixed-point adjoint (adjoint_mode 1) needs obj_window 0: J = F(f^N)");
@@ -596,6 +649,7 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   k.nz = p.nz;
   k.nscal = p.nscalars;
   k.N = h->N;
+  k.wait_polls = -1;
   k.fd_nx = albm::make_fastdiv((unsigned)p.nx);
   k.fd_ny = albm::make_fastdiv((unsigned)p.ny);
   k.fd_hx = albm::make_fastdiv((unsigned)std::max(p.nx / 2, 1));
@@ -611,6 +665,10 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   k.rho_out = (float)p.rho_out;
   k.drho_out = (float)(p.rho_out - 1.0);
   k.one_m_rho_out = (float)(1.0 - p.rho_out);
+  k.inlet_kind = p.inlet_kind;
+  k.rho_in = (float)(p.rho_out + 3.0 * p.dp);
+  k.drho_in = (float)(p.rho_out + 3.0 * p.dp - 1.0);
+  k.inv_rho_in = (float)(1.0 / (p.rho_out + 3.0 * p.dp));
   k.alpha_f = (float)p.alpha_fluid;
   k.alpha_s = (float)p.alpha_solid;
   k.porosity = p.porosity;
@@ -631,10 +689,8 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   }
   h->state_bytes = (size_t)h->M * (size_t)h->N * (size_t)h->ks.storage_bytes;
   h->state_stride = (h->state_bytes + 255) / 256 * 256;
-  // states below 2 MiB (the granularity of cudaMalloc's mappings) are
-  // carved out of 32 MiB slabs, so that a pool of many small states costs
-  // its bytes and not a page per state
-  h->slab_states = h->state_stride < (2u << 20) ? (int)((32u << 20) / h->state_stride) : 1;
+  // states are carved out of slabs of up to about 1 GiB (at least one state)
+  h->slab_states = (int)std::max<size_t>(1, std::min<size_t>(4096, (1ull << 30) / h->state_stride));
   // time weights c_n of J = sum_n c_n F(f^n)
   h->c.assign((size_t)p.nsteps + 1, 0.0);
   if (p.objective != LBM_OBJ_NONE) {
@@ -651,6 +707,12 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   if (e != cudaSuccess) {
     h->err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
     return fail(LBM_ERR_CUDA);
+  }
+  e = h->ks.preload();
+  if (e == cudaSuccess) e = preload_runtime_kernels();
+  if (e != cudaSuccess) {
+    h->err = std::string("loading the kernels: ") + cudaGetErrorString(e);
+    return fail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA);
   }
   // device arrays
 #define CKC(call)                                                            \
@@ -722,6 +784,7 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
   if (p.ckpt_every > 0) h->ckpt = p.ckpt_every;
   else if (p.nsteps + 2 <= h->max_bufs) h->ckpt = 1;
   else h->ckpt = std::max(1, (p.nsteps + h->max_bufs / 2 - 1) / std::max(1, h->max_bufs / 2));
+  h->time_buf.assign((size_t)p.nsteps + 2, -1);
   CKC(cudaEventCreate(&h->t0));
   CKC(cudaEventCreate(&h->t1));
   CKC(cudaEventCreate(&h->t2));
@@ -736,8 +799,6 @@ lbm_status lbm_create(lbm_handle* out, const lbm_params* pp, const float* theta,
 void lbm_destroy(lbm_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (size_t i = 0; i < h->bufs.size(); ++i)
-    if (!h->buf_in_slab[i]) cudaFree(h->bufs[i]);
   for (void* b : h->slabs) cudaFree(b);
   cudaFree(h->flags);
   cudaFree(h->theta);
@@ -790,7 +851,7 @@ lbm_status lbm_primal_step(lbm_handle h, int k) {
     if (s) return s;
     s = launch_primal(h, src, dst, h->t, true, K_PRIMAL);
     if (s) return s;
-    h->buf_time[dst] = h->t + 1;  // f^t stays while the pool has room
+    set_time(h, dst, h->t + 1);  // f^t stays while the pool has room
     h->t += 1;
   }
   if (k > 0 && h->t == h->p.nsteps) {
@@ -912,8 +973,7 @@ lbm_status lbm_adjoint_step(lbm_handle h, int k) {
   for (int i = 0; i < k; ++i) {
     const int n = h->t_adj - 1;
     // states newer than n are no longer needed
-    for (size_t b = 0; b < h->bufs.size(); ++b)
-      if (h->buf_time[b] > n) h->buf_time[b] = -1;
+    while (!h->held.empty() && *h->held.rbegin() > n) set_time(h, h->time_buf[*h->held.rbegin()], -1);
     lbm_status s = ensure_state(h, n);
     if (s) return s;
     s = launch_adjoint(h, n, 1);
@@ -1041,10 +1101,10 @@ static lbm_status batch_primal(const lbm_handle* hs, int n, const int* ks, int k
     auto unwind = [&](lbm_ctx* hf, lbm_status s) {
       for (auto& m : moved) {
         if (m.alone) {
-          m.h->buf_time[m.dst] = m.h->t + 1;
+          set_time(m.h, m.dst, m.h->t + 1);
           m.h->t += 1;
         } else if (m.h->buf_time[m.dst] == -2) {
-          m.h->buf_time[m.dst] = -1;
+          set_time(m.h, m.dst, -1);
         }
       }
       return batch_fail(hs[0], hf, s);
@@ -1062,7 +1122,7 @@ static lbm_status batch_primal(const lbm_handle* hs, int n, const int* ks, int k
         moved.push_back({h, src, dst, true});
         continue;
       }
-      h->buf_time[dst] = -2;  // reserved until the launch is issued
+      // dst stays reserved (-2) until the launch is issued
       albm::InstanceDesc& D = args.inst[args.n++];
       memset(&D, 0, sizeof(D));
       D.P = h->kp;
@@ -1092,7 +1152,7 @@ static lbm_status batch_primal(const lbm_handle* hs, int n, const int* ks, int k
         lbm_status s = fold_objective(h, h->t, (h->N + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK);
         if (s) return batch_fail(hs[0], h, s);
       }
-      h->buf_time[m.dst] = h->t + 1;
+      set_time(h, m.dst, h->t + 1);
       h->t += 1;
       if (h->t == h->p.nsteps) {
         lbm_status s = record_final_objective(h);
@@ -1144,8 +1204,8 @@ static lbm_status batch_adjoint(const lbm_handle* hs, int n, const int* ks, int 
       lbm_ctx* h = hs[i];
       if (h->t_adj <= stop[(size_t)i]) continue;  // adjoint finished or this call's steps done
       const int nn = h->t_adj - 1;
-      for (size_t b = 0; b < h->bufs.size(); ++b)
-        if (h->buf_time[b] > nn) h->buf_time[b] = -1;
+      while (!h->held.empty() && *h->held.rbegin() > nn)
+        set_time(h, h->time_buf[*h->held.rbegin()], -1);
       lbm_status s = ensure_state(h, nn);
       if (s) return batch_fail(hs[0], h, s);
       any = true;
@@ -1253,7 +1313,7 @@ lbm_status lbm_get_populations_at(lbm_handle h, int time, float* dst, int which)
 
 lbm_status lbm_set_populations(lbm_handle h, const float* src) {
   if (!h || !src) return LBM_ERR_ARG;
-  for (auto& t : h->buf_time) t = -1;
+  reset_pool(h);
   int b;
   lbm_status s = acquire(h, &b);
   if (s) return s;
@@ -1275,7 +1335,7 @@ lbm_status lbm_set_populations(lbm_handle h, const float* src) {
     cudaFree(tmp);
   }
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "import: %s", cudaGetErrorString(e));
-  h->buf_time[b] = 0;
+  set_time(h, b, 0);
   h->t = 0;
   h->t_adj = h->oneshot ? 0 : -1;
   CK(h, cudaMemsetAsync(h->stats, 0, sizeof(double) * 2 * (size_t)(h->p.nsteps + 1), h->stream));
@@ -1317,6 +1377,12 @@ lbm_status lbm_check_finite(lbm_handle h, long long* count) {
   }
   *count = (long long)c;
   if (c) FAIL(h, LBM_ERR_NONFINITE, "%llu non-finite values in the state at time %d", c, h->t);
+  return LBM_OK;
+}
+
+lbm_status lbm_set_wait_polls(lbm_handle h, long long polls) {
+  if (!h) return LBM_ERR_ARG;
+  h->kp.wait_polls = polls < 0 ? -1 : (int)std::min<long long>(polls, 1LL << 30);
   return LBM_OK;
 }
 
@@ -1453,8 +1519,8 @@ static lbm_status oneshot_iteration(lbm_ctx* h, double zeta, double penalty, dou
   prof_end(h, slot);
   if (e != cudaSuccess) FAIL(h, LBM_ERR_CUDA, "adjoint kernel launch: %s", cudaGetErrorString(e));
   h->lam_cur = 1 - h->lam_cur;
-  h->buf_time[src] = -1;
-  h->buf_time[dst] = 0;
+  set_time(h, src, -1);
+  set_time(h, dst, 0);
   return LBM_OK;
 }
 
@@ -1555,8 +1621,8 @@ lbm_status lbm_threshold_scan(lbm_handle h, const double* eta, int n, int nsteps
       result = acquire(h, &dst);
       if (result) break;
       result = launch_primal(h, cur, dst, 0, false, K_PRIMAL);
-      h->buf_time[cur] = -1;
-      h->buf_time[dst] = 0;
+      set_time(h, cur, -1);
+      set_time(h, dst, 0);
       cur = dst;
     }
     if (result == LBM_OK) result = state_objective(h, cur);

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "albm_node.cuh"
 
 namespace albm {
@@ -713,6 +715,7 @@ struct KernelSet {
   cudaError_t (*importf)(const KParams&, const StepArgs&, cudaStream_t);
   cudaError_t (*nonfinite)(const KParams&, const StepArgs&, int M, cudaStream_t);
   cudaError_t (*rest)(const KParams&, const StepArgs&, cudaStream_t);
+  cudaError_t (*preload)();  // load every kernel of the set on the current device
   cudaError_t (*primal_batch)(const BatchArgs&, long long blocks, cudaStream_t);
   cudaError_t (*adjoint_batch)(const BatchArgs&, long long blocks, cudaStream_t);
   cudaError_t (*primal_tiles)(const KParams&, const StepArgs&, cudaStream_t);
@@ -871,13 +874,53 @@ struct Launch {
                                        a.grad, a.ws, a.stat_n, a.has_next);
     return cudaGetLastError();
   }
+  // With lazy module loading a kernel is loaded at its first launch, which
+  // allocates device memory: a launch late in a run, when state pools have
+  // taken the memory, could fail.  Querying every kernel's attributes loads
+  // them all while the handle is created.
+  static cudaError_t preload() {
+    static std::atomic<unsigned long long> done{0};   // one bit per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return cudaSuccess;
+    cudaFuncAttributes fa;
+    const void* ks[] = {
+        (const void*)primal_kernel<L, NS, MRT, S, 0>, (const void*)primal_kernel<L, NS, MRT, S, 1>,
+        (const void*)primal_kernel<L, NS, MRT, S, 2>, (const void*)objective_kernel<L, NS, MRT, S>,
+        (const void*)adjoint_kernel<L, NS, MRT, S, 0>, (const void*)adjoint_kernel<L, NS, MRT, S, 1>,
+        (const void*)adjoint_kernel<L, NS, MRT, S, 2>, (const void*)export_kernel<L, NS, S>,
+        (const void*)import_kernel<L, NS, S>, (const void*)rest_kernel<L, NS, S>,
+        (const void*)nonfinite_kernel<S>, (const void*)primal_batch_kernel<L, NS, MRT, S>,
+        (const void*)adjoint_batch_kernel<L, NS, MRT, S>,
+        (const void*)primal_tiles_kernel<L, NS, MRT, S, kTile>,
+        (const void*)adjoint_tiles_kernel<L, NS, MRT, S, kTile>,
+        (const void*)primal_async_kernel<L, NS, MRT, S, kTile>,
+        (const void*)adjoint_async_kernel<L, NS, MRT, S, kTile>};
+    for (const void* k : ks) {
+      e = cudaFuncGetAttributes(&fa, k);
+      if (e != cudaSuccess) return e;
+    }
+    if constexpr (sizeof(S) == 2) {
+      const void* kp[] = {(const void*)primal_pair_kernel<L, NS, MRT, S, 0>,
+                          (const void*)primal_pair_kernel<L, NS, MRT, S, 1>,
+                          (const void*)primal_pair_kernel<L, NS, MRT, S, 2>};
+      for (const void* k : kp) {
+        e = cudaFuncGetAttributes(&fa, k);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    done.fetch_or(bit);
+    return cudaSuccess;
+  }
   static long long primal_partials(const KParams& P) {
     const long long threads = paired(P) ? P.N / 2 : P.N;
     return (threads + ALBM_PRIMAL_BLOCK - 1) / ALBM_PRIMAL_BLOCK;
   }
   static KernelSet set() {
     return KernelSet{&primal, &objective, &adjoint, &exportf, &importf, &nonfinite, &rest,
-                     &primal_batch, &adjoint_batch, &primal_tiles, &adjoint_tiles,
+                     &preload, &primal_batch, &adjoint_batch, &primal_tiles, &adjoint_tiles,
                      &primal_async, &adjoint_async, &primal_partials, (int)sizeof(S)};
   }
 };

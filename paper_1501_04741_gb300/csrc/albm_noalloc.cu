@@ -201,6 +201,9 @@ extern "C" lbm_status lbm_state_objective_noalloc(const lbm_params* pp, const fl
   if (p.inlet_outlet && (p.nx < 3 || !(p.u_in < 1.0) || !(p.rho_out > 0.0)))
     return fail(LBM_ERR_ARG, "inlet_outlet needs nx >= 3, u_in < 1 and rho_out > 0");
   if (p.porosity < 0 || p.porosity > 2) return fail(LBM_ERR_ARG, "unknown porosity law");
+  if (p.inlet_kind < 0 || p.inlet_kind > 1 ||
+      (p.inlet_kind == 1 && !(p.rho_out + 3.0 * p.dp > 0.0)))
+    return fail(LBM_ERR_ARG, "bad inlet kind or pressure drop");
   if (p.scalar_inlet < 0 || p.scalar_inlet > 2)
     return fail(LBM_ERR_ARG, "unknown scalar inlet profile");
   const long long N = (long long)p.nx * p.ny * p.nz;
@@ -250,6 +253,10 @@ extern "C" lbm_status lbm_state_objective_noalloc(const lbm_params* pp, const fl
   P.rho_out = (float)p.rho_out;
   P.drho_out = (float)(p.rho_out - 1.0);
   P.one_m_rho_out = (float)(1.0 - p.rho_out);
+  P.inlet_kind = p.inlet_kind;
+  P.rho_in = (float)(p.rho_out + 3.0 * p.dp);
+  P.drho_in = (float)(p.rho_out + 3.0 * p.dp - 1.0);
+  P.inv_rho_in = (float)(1.0 / (p.rho_out + 3.0 * p.dp));
   P.alpha_f = (float)p.alpha_fluid;
   P.alpha_s = (float)p.alpha_solid;
   P.porosity = p.porosity;

@@ -113,6 +113,8 @@ struct KParams {
   float omega, one_m_omega, nu;
   float gx, gy, gz;
   float u_in, inv_1m_uin, rho_out, drho_out, one_m_rho_out;
+  int inlet_kind;        // 0 velocity inlet at u_in; 1 pressure inlet at rho_in, capped at u_in
+  float rho_in, drho_in, inv_rho_in;
   float alpha_f, alpha_s;
   int porosity;
   float por_q;
@@ -128,6 +130,8 @@ struct KParams {
   float dev_off[19];
   // n / nx, n / ny and n / (nx / 2) for node, row and pair indices (N < 2^31)
   FastDiv fd_nx, fd_ny, fd_hx;
+  // polls a tile-staged kernel waits for a stage's copies (< 0: default)
+  int wait_polls;
 };
 
 // MRT coefficients of NodeOps::mrt_op for rates omega (stress moments),
@@ -318,8 +322,18 @@ struct NodeOps {
   // each unknown is its opposite plus 2 w_i rho (e_i.u) / cs2, minus the
   // transverse correction sum_t e_it N_t, N_t = 1/2 sum_{e.n = 0} f_k e_kt.
   // In deviations the weights cancel: s0 + 2 s_out = 1 + D0 + 2 D_out.
+  // The inlet is a velocity face (u = u_in, rho from the balance) or, for a
+  // pressure inlet (Sec. 4), a pressure face (rho = rho_in, u = 1 - (1 + D0 +
+  // 2 D_out) / rho_in) as long as that u stays within the cap u_in, else a
+  // velocity face at the cap; pface reports a pressure face (the outlet
+  // always is one).
   __device__ static __forceinline__ void zou_he(const KParams& P, bool inlet, float* d, float& rho,
                                                 float& drho, float* u) {
+    bool pface;
+    zou_he(P, inlet, d, rho, drho, u, pface);
+  }
+  __device__ static __forceinline__ void zou_he(const KParams& P, bool inlet, float* d, float& rho,
+                                                float& drho, float* u, bool& pface) {
     float D0 = 0.0f, Dout = 0.0f, Ny = 0.0f, Nz = 0.0f;
     const int sgn = inlet ? 1 : -1;  // inward normal along x
 #pragma unroll
@@ -336,10 +350,23 @@ struct NodeOps {
     Ny *= 0.5f;
     Nz *= 0.5f;
     if (inlet) {
-      drho = (D0 + 2.0f * Dout + P.u_in) * P.inv_1m_uin;
-      rho = 1.0f + drho;
-      u[0] = P.u_in;
+      pface = false;
+      if (P.inlet_kind == 1) {
+        const float up = (P.drho_in - D0 - 2.0f * Dout) * P.inv_rho_in;
+        if (up <= P.u_in) {
+          pface = true;
+          rho = P.rho_in;
+          drho = P.drho_in;
+          u[0] = up;
+        }
+      }
+      if (!pface) {
+        drho = (D0 + 2.0f * Dout + P.u_in) * P.inv_1m_uin;
+        rho = 1.0f + drho;
+        u[0] = P.u_in;
+      }
     } else {
+      pface = true;
       rho = P.rho_out;
       drho = P.drho_out;
       u[0] = (D0 + 2.0f * Dout + P.one_m_rho_out) / P.rho_out;
@@ -564,7 +591,7 @@ struct NodeOps {
         const float c = inlet_value(P, s, y);
 #pragma unroll
         for (int i = 0; i < QS; ++i)
-          g[s][i] = LS::w(i) * c * (1.0f + float(LS::ex(i)) * P.u_in * (1.0f / LS::cs2));
+          g[s][i] = LS::w(i) * c * (1.0f + float(LS::ex(i)) * u[0] * (1.0f / LS::cs2));
         continue;
       }
       float T, den;
@@ -676,10 +703,11 @@ struct NodeOps {
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = d_in[i];
     float rho, drho, u[3];
+    bool pface = false;   // the face of a boundary node holds rho (u follows)
     if (type == INLET) {
-      zou_he(P, true, d, rho, drho, u);
+      zou_he(P, true, d, rho, drho, u, pface);
     } else if (type == OUTLET) {
-      zou_he(P, false, d, rho, drho, u);
+      zou_he(P, false, d, rho, drho, u, pface);
     } else {
       moments(d, rho, drho, u);
     }
@@ -754,9 +782,17 @@ struct NodeOps {
 #endif
     load(a, b);
     // ---- scalar lattices ----
+    float du_in = 0.0f;   // d(objective)/d(u_x) through the inlet scalars of a pressure face
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       if (type == INLET) {
+        if (pface) {
+          // g_i = w_i c (1 + e_ix u_x / cs2) with the face velocity u_x
+          const float c = inlet_value(P, s, y);
+#pragma unroll
+          for (int k = 0; k < QS; ++k)
+            if (LS::ex(k)) du_in += b[s][k] * (LS::w(k) * c * float(LS::ex(k)) * (1.0f / LS::cs2));
+        }
 #pragma unroll
         for (int k = 0; k < QS; ++k) lamg[s][k] = 0.0f;
         continue;
@@ -924,21 +960,23 @@ struct NodeOps {
     // ---- Zou-He transpose ----
     const bool inlet = (type == INLET);
     const int sgn = inlet ? 1 : -1;
-    // total sensitivity of the face scalar (rho at the inlet, u_x at the outlet)
-    float dface = inlet ? ddrho : du[0];
+    // total sensitivity of the face's free scalar: rho on a velocity face,
+    // u_x on a pressure face (the outlet, an uncapped pressure inlet)
+    float dface = pface ? du[0] + du_in : ddrho;
     float dNy = 0.0f, dNz = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (L::ex(i) * sgn > 0) {
         const float coef = 6.0f * L::w(i) * float(L::ex(i));
-        dface += lam[i] * coef * (inlet ? u[0] : rho);
+        dface += lam[i] * coef * (pface ? rho : u[0]);
         if (L::ey(i)) dNy -= lam[i] * float(L::ey(i));
         if (L::ez(i)) dNz -= lam[i] * float(L::ez(i));
       }
     }
-    // d(face scalar)/d(D0) and /d(Dout): 1/(1-u_in), 2/(1-u_in) at the inlet;
-    // 1/rho_out, 2/rho_out at the outlet
-    const float k1 = inlet ? P.inv_1m_uin : 1.0f / P.rho_out;
+    // d(face scalar)/d(D0) and /d(Dout) = k1, 2 k1: velocity face rho = (1 +
+    // D0 + 2 Dout) / (1 - u_in); outlet u_x = (1 + D0 + 2 Dout) / rho_out - 1;
+    // pressure inlet u_x = 1 - (1 + D0 + 2 Dout) / rho_in
+    const float k1 = !pface ? P.inv_1m_uin : (inlet ? -P.inv_rho_in : 1.0f / P.rho_out);
     float out[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {

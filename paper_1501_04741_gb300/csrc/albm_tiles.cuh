@@ -17,7 +17,7 @@
 //
 // Every wait on an mbarrier is bounded: if a stage does not complete within
 // the limit, the block records an error (LBM_ERR_TIMEOUT on the host), waits
-// with a bound for its other copy in flight and returns.
+// with a bound for both stages' copies still in flight and returns.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -55,11 +55,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   return ok != 0;
 }
 
-// bounded: about 2^22 polls (each poll may suspend the thread for a while)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-  for (int i = 0; i < (1 << 22); ++i)
+// Waits are bounded by a number of polls (each poll may suspend the thread
+// for a while): KParams.wait_polls for a stage the block is about to use
+// (negative: the default), kDrainPolls when a block that gave up drains the
+// copies it still has in flight before it leaves.
+constexpr long long kDrainPolls = 1LL << 22;
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, long long polls) {
+  for (long long i = 0; i < polls; ++i)
     if (mbar_try_wait(bar, phase)) return true;
   return false;
+}
+
+__device__ __forceinline__ long long stage_polls(const KParams& P) {
+  return P.wait_polls < 0 ? kDrainPolls : (long long)P.wait_polls;
 }
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -173,10 +182,12 @@ __global__ void __launch_bounds__(TX) primal_tiles_kernel(KParams P, const S* __
     const int sg = it & 1;
     const long long tn = t + gridDim.x;
     if (tn < ntiles) issue(tn, sg ^ 1);
-    const bool ok = mbar_wait(&bar[sg], phase[sg]);
+    const bool ok = mbar_wait(&bar[sg], phase[sg], stage_polls(P));
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicExch(err, 1);
-      if (tn < ntiles) mbar_wait(&bar[sg ^ 1], phase[sg ^ 1]);
+      // leave no copy in flight: drain the stage given up on and the next one
+      mbar_wait(&bar[sg], phase[sg], kDrainPolls);
+      if (tn < ntiles) mbar_wait(&bar[sg ^ 1], phase[sg ^ 1], kDrainPolls);
       return;
     }
     phase[sg] ^= 1u;
@@ -272,10 +283,12 @@ __global__ void __launch_bounds__(TX) adjoint_tiles_kernel(
     const int sg = it & 1;
     const long long tn = t + gridDim.x;
     if (tn < ntiles) issue(tn, sg ^ 1);
-    const bool ok = mbar_wait(&bar[sg], phase[sg]);
+    const bool ok = mbar_wait(&bar[sg], phase[sg], stage_polls(P));
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicExch(err, 1);
-      if (tn < ntiles) mbar_wait(&bar[sg ^ 1], phase[sg ^ 1]);
+      // leave no copy in flight: drain the stage given up on and the next one
+      mbar_wait(&bar[sg], phase[sg], kDrainPolls);
+      if (tn < ntiles) mbar_wait(&bar[sg ^ 1], phase[sg ^ 1], kDrainPolls);
       return;
     }
     phase[sg] ^= 1u;

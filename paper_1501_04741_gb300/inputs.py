@@ -47,7 +47,10 @@ class Problem:
     force: tuple = (0.0, 0.0, 0.0)   # body acceleration g (EDM forcing, Sec. 3.1)
     walls: str = "y"                 # axes carrying bounce-back wall planes at both ends
     channel: str = "periodic"        # "periodic" in x | "inlet_outlet" (Zou-He x faces)
-    u_in: float = 0.05               # velocity inlet speed (x = 0 face)
+    inlet: str = "velocity"          # "velocity": u = u_in | "pressure": rho = rho_out + 3 dp
+    #                                  with the inlet velocity capped at u_in (Sec. 4)
+    dp: float = 0.0                  # pressure drop of a pressure inlet (lattice units)
+    u_in: float = 0.05               # velocity inlet speed (x = 0 face), or its cap
     rho_out: float = 1.0             # pressure outlet density (x = Lx-1 face)
     nscalars: int = 0                # passive scalar lattices (D3Q7 in 3D, D2Q9 in 2D)
     alpha_fluid: float = 0.0         # scalar diffusivity in fluid (theta = 0)
@@ -152,14 +155,14 @@ def paper_mixer_empty(**kw) -> Problem:
     """The paper's mixing channel without obstacle (Tab. tab:cases, Sec. 4.1):
     D3Q19 MRT 450x50x50, nu = 0.02 (tau = 0.56), one D3Q7 scalar with
     alpha = 0.003 in both phases, inlet T = -1 for y < 25 and +1 above,
-    objective the outlet mixing flux of Eq. mixing:obj, theta = 0.  The
-    paper drives the channel by a pressure drop of 0.016666 with the inlet
-    velocity limited to 0.05; the empty channel would carry more, so the
-    limit holds and the inlet runs as a velocity inlet at 0.05.  40 000
-    steps (the iterations Tab. tab:results lists for the empty mixer)."""
+    objective the outlet mixing flux of Eq. mixing:obj, theta = 0.  Driven
+    by the pressure drop 0.016666 between inlet and outlet (Sec. 4), with
+    the inlet velocity limited to 0.05.  40 000 steps (the iterations
+    Tab. tab:results lists for the empty mixer)."""
     nu = 0.02
     p = Problem(lattice="D3Q19", dims=(450, 50, 50), collision="MRT", tau=3 * nu + 0.5,
-                walls="yz", channel="inlet_outlet", u_in=0.05, rho_out=1.0,
+                walls="yz", channel="inlet_outlet", inlet="pressure", dp=0.016666,
+                u_in=0.05, rho_out=1.0,
                 nscalars=1, alpha_fluid=0.003, alpha_solid=0.003, scalar_inlet="signed",
                 objective="mixflux", obj_window=0, nsteps=40000,
                 design=(61, 391, 1, 49, 1, 49), ckpt_every=0)
@@ -171,13 +174,15 @@ def paper_exchanger_empty(**kw) -> Problem:
     Sec. 4.2): D3Q19 MRT 352x50x50, nu = 0.01 (tau = 0.53), one D3Q7
     temperature with alpha = 0.003 in the fluid and 1 in the solid, inlet
     T = 0, a D x D plate at T = 1 on the bottom wall in the middle, objective
-    the outlet heat flux of Eq. exchanger:obj, theta = 0.  Inlet at the
-    velocity limit 0.05 (as for the mixer); 30 000 steps (Tab. tab:results)."""
+    the outlet heat flux of Eq. exchanger:obj, theta = 0.  Driven by the
+    pressure drop 0.03 (Sec. 4) with the inlet velocity limited to 0.05;
+    30 000 steps (Tab. tab:results)."""
     nu = 0.01
     Lx, Ly, Lz = 352, 50, 50
     x0 = Lx // 2 - Ly // 2
     p = Problem(lattice="D3Q19", dims=(Lx, Ly, Lz), collision="MRT", tau=3 * nu + 0.5,
-                walls="yz", channel="inlet_outlet", u_in=0.05, rho_out=1.0,
+                walls="yz", channel="inlet_outlet", inlet="pressure", dp=0.03,
+                u_in=0.05, rho_out=1.0,
                 nscalars=1, alpha_fluid=0.003, alpha_solid=1.0, scalar_inlet="zero",
                 hot=(x0, x0 + Ly, 0, Lz), T_hot=1.0, objective="heatflux", obj_window=0,
                 nsteps=30000, design=(101, 253, 1, 49, 1, 49), ckpt_every=0)
@@ -213,6 +218,38 @@ def scaled(p: Problem, dims, nsteps=None, **kw) -> Problem:
 # ---------------------------------------------------------------------------
 # Seeded porosity fields (FP32, the same bytes go to both implementations)
 # ---------------------------------------------------------------------------
+
+def fins_theta(p: Problem, n: int, width: int, min_gap: int = 3) -> np.ndarray:
+    """The finned exchanger of Sec. 4.2: `n` evenly spaced parallel plates of
+    thickness `width` (z) standing on the heating plate, spanning its length
+    (x over the hot patch) and the channel's interior height (y); theta = 1
+    (solid, with the solid diffusivity) on the plates, 0 elsewhere.  Raises
+    ValueError when the gaps between the plates and the walls fall below
+    `min_gap` nodes.  Returns float32 (Lz, Ly, Lx)."""
+    Lx, Ly, Lz = p.dims
+    if not p.hot:
+        raise ValueError("the finned exchanger needs a hot patch")
+    x0, x1 = p.hot[0], p.hot[1]
+    span = Lz - 2                                  # interior nodes across z
+    gap = (span - n * width) / (n + 1)
+    if n < 1 or width < 1 or gap < min_gap:
+        raise ValueError(f"{n} fins of width {width} leave gaps of {gap:.2f} < {min_gap}")
+    th = np.zeros((Lz, Ly, Lx), dtype=np.float32)
+    for k in range(n):
+        z0 = 1 + int(round(gap * (k + 1) + width * k))
+        th[z0:z0 + width, 1:Ly - 1, x0:x1] = 1.0
+    return th
+
+
+def fin_sweep(p: Problem, counts=range(1, 8), widths=range(3, 11), min_gap: int = 3):
+    """(n, width) pairs of the fin study of Sec. 4.2 that keep the gaps."""
+    out = []
+    for n in counts:
+        for w in widths:
+            if (p.dims[2] - 2 - n * w) / (n + 1) >= min_gap:
+                out.append((n, w))
+    return out
+
 
 def design_mask(p: Problem) -> np.ndarray:
     """Boolean (Lz, Ly, Lx) mask of the design box."""

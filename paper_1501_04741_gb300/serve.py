@@ -50,7 +50,7 @@ def densities(P: Problem) -> int:
 
 
 # device allocations are charged in whole 2 MiB pages, the granularity of
-# cudaMalloc's mappings (the library carves small states out of larger
+# cudaMalloc's mappings (the library carves the pool's states out of larger
 # slabs, so the pool itself costs its bytes plus at most one page)
 ALLOC_GRANULE = 2 << 20
 
@@ -129,7 +129,7 @@ def _percentiles(lat):
 class Server:
     def __init__(self, reserve_bytes: float = 4 << 30, capacity_bytes: float | None = None,
                  steps_per_tick: int = 200, work_per_tick: float = 2e7, max_states: int = 48,
-                 pool_fraction: float = 0.25, stream=None,
+                 pool_fraction: float = 0.05, stream=None,
                  mem_get_info=None, keep_gradients: bool = True, solver_factory=None,
                  primal_fn=None, adjoint_fn=None):
         # the factories exist so that the scheduling can run against a fake

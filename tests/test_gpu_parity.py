@@ -53,6 +53,9 @@ def _cases():
                                                nsteps=40),
         "d3q19_mrt_paper_exchanger": inputs.scaled(inputs.paper_exchanger_empty(), (14, 10, 9),
                                                    nsteps=120),
+        # the pressure inlet below its velocity cap throughout
+        "d3q19_bgk_exchanger_pressure_open": exch.replace(inlet="pressure", dp=0.003,
+                                                          objective="heatflux_dp"),
     }
 
 

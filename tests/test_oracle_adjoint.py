@@ -29,6 +29,12 @@ def _cases():
         "paper_mixer_signed": inputs.scaled(inputs.paper_mixer_empty(), (10, 6, 6), nsteps=16),
         "paper_exchanger_heatflux": inputs.scaled(inputs.paper_exchanger_empty(), (12, 6, 6),
                                                   nsteps=16),
+        # the paper's pressure inlet: above the velocity cap (dp = 0.03 drives
+        # the short channel faster than 0.05) and below it
+        "exchanger_pressure_capped": inputs.scaled(inputs.paper_exchanger_empty(), (12, 6, 6),
+                                                   nsteps=16).replace(inlet="pressure", dp=0.03),
+        "exchanger_pressure_open": inputs.scaled(inputs.paper_exchanger_empty(), (12, 6, 6),
+                                                 nsteps=16).replace(inlet="pressure", dp=0.004),
     }
 
 

@@ -314,3 +314,26 @@ def test_outlet_scalar_with_pre_collision_sign_is_caught(monkeypatch):
     for lat in ("D2Q9", "D3Q19"):
         with pytest.raises(AssertionError):
             TP.test_outlet_scalar_reconstruction_worked_example(lat)
+
+
+def test_pressure_inlet_without_the_cap_is_caught(monkeypatch):
+    def uncapped(self, f):
+        return self.zou_he(f, +1, rho=self.P.rho_out + self.P.dp / self.fl.cs2)[0]
+    _mutate(monkeypatch, "inlet", uncapped)
+    with pytest.raises(AssertionError):
+        TP.test_pressure_inlet_prescribed_values("D3Q19")
+
+
+def test_pressure_inlet_density_without_cs2_is_caught(monkeypatch):
+    orig = om.Model.inlet
+
+    def bad(self, f):
+        saved = self.P
+        self.P = saved.replace(dp=saved.dp / 3.0)       # rho_in = rho_out + dp
+        try:
+            return orig(self, f)
+        finally:
+            self.P = saved
+    _mutate(monkeypatch, "inlet", bad)
+    with pytest.raises(AssertionError):
+        TP.test_pressure_inlet_prescribed_values("D2Q9")

@@ -430,8 +430,8 @@ def test_outlet_variance_of_a_two_level_profile():
 
 def test_paper_presets_follow_the_printed_cases():
     # inputs.paper_*_empty carry Tab. tab:cases: sizes, nu (tau = 3 nu + 1/2),
-    # the diffusivities and the design span (nodes x_first..x_last); the
-    # pressure drop is not an input (the inlet runs at its velocity limit).
+    # the diffusivities, the design span (nodes x_first..x_last) and the
+    # pressure drop of the pressure inlet, whose velocity limit is 0.05 (Sec. 4).
     import os
     path = os.path.join(os.path.dirname(__file__), "golden", "paper_table_cases.txt")
     rows = {}
@@ -447,6 +447,7 @@ def test_paper_presets_follow_the_printed_cases():
         assert P.alpha_fluid == a_f and P.alpha_solid == a_s
         assert P.design[0] == int(x0) and P.design[1] == int(x1) + 1
         assert P.u_in == 0.05 and P.collision == "MRT" and P.nscalars == 1
+        assert P.inlet == "pressure" and P.dp == dp and P.rho_out == 1.0
 
 
 
@@ -552,3 +553,53 @@ def test_outlet_scalar_reconstruction_worked_example(lattice):
     # the heat flux of this node is v_x T*
     assert abs(float(o.model.objective(F, torch.zeros(1, dtype=torch.float64), flags,
                                        torch.zeros(1, dtype=torch.long))) - ux * T_star) <= 1e-15
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19"])
+def test_pressure_inlet_prescribed_values(lattice):
+    # Zou-He pressure inlet with the velocity cap of Sec. 4, at one node whose
+    # incoming populations are those of the equilibrium at rho = 1.02, u =
+    # (0.03, 0, 0): mass and normal momentum give s0 + 2 s_out = rho (1 - u)
+    # = 0.9894.  With dp = 0.03 (rho_in = 1.09) the pressure condition would
+    # give u = 1 - 0.9894 / 1.09 = 0.0923 > 0.05, so the node is a velocity
+    # inlet at the cap: u = 0.05, rho = 0.9894 / 0.95.  With dp = 0.001
+    # (rho_in = 1.003) it stays a pressure inlet: rho = 1.003, u = 1 -
+    # 0.9894 / 1.003.  Either way the reconstructed node carries that mass
+    # and normal momentum, with no transverse momentum.
+    dims = (3, 1, 1)
+    for dp, rho_want, u_want in ((0.03, 0.9894 / 0.95, 0.05),
+                                 (0.001, 1.003, 1.0 - 0.9894 / 1.003)):
+        P = inputs.Problem(lattice=lattice, dims=dims, collision="BGK", tau=0.8, walls="",
+                           channel="inlet_outlet", inlet="pressure", dp=dp, u_in=0.05,
+                           rho_out=1.0, objective="none")
+        o = Oracle(P, np.zeros(dims[::-1], np.float32))
+        m = o.model
+        E = m.E.numpy()
+        eu = E[:, 0] * 0.03
+        f = 1.02 * m.w.numpy() * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * 0.03 ** 2)
+        F = torch.tensor(f, dtype=torch.float64)[:, None]
+        mac = m.macroscopic(F, torch.zeros(1, dtype=torch.float64), torch.tensor([INLET]))
+        fr = mac["fr"][:, 0].numpy()
+        assert abs(fr.sum() - rho_want) <= 1e-14
+        assert abs((E[:, 0] * fr).sum() - rho_want * u_want) <= 1e-14
+        assert abs((E[:, 1] * fr).sum()) <= 1e-15 and abs((E[:, 2] * fr).sum()) <= 1e-15
+        assert abs(float(mac["rho"][0]) - rho_want) <= 1e-14
+        assert abs(float(mac["u"][0, 0]) - u_want) <= 1e-14
+
+
+def test_pressure_driven_channel_carries_the_inlet_density():
+    # a short pressure-driven channel below the cap: every inlet node holds
+    # rho_in exactly after its reconstruction, and the flow runs from the
+    # inlet to the outlet
+    P = inputs.Problem(lattice="D3Q19", dims=(16, 7, 7), collision="BGK", tau=0.8, walls="yz",
+                       channel="inlet_outlet", inlet="pressure", dp=0.002, u_in=0.05,
+                       rho_out=1.0, objective="none", nsteps=200)
+    o = Oracle(P, np.zeros((7, 7, 16), np.float32))
+    _, traj = o.primal(keep=False)
+    F = traj[-1].reshape(o.model.M, -1)
+    mac = o.model.macroscopic(F, o.theta, o.flags)
+    inl = (o.flags == INLET) & (mac["u"][0] <= P.u_in)
+    assert int(inl.sum()) > 0
+    assert float((mac["rho"][inl] - (1.0 + 3 * P.dp)).abs().max()) <= 1e-12
+    fl = o.flags == FLUID
+    assert float(mac["u"][0][fl].mean()) > 0.0
