@@ -52,9 +52,11 @@ namespace albm {
 #ifndef ALBM_ADJ_BLOCK
 #define ALBM_ADJ_BLOCK 64
 #endif
-// resident blocks of the adjoint kernel without objective sources
+// resident blocks of the adjoint kernel without objective sources: 10 holds
+// the mixer's (MRT, two scalars) at 96 registers, which the inlet branches
+// would otherwise raise to 104 (9 blocks)
 #ifndef ALBM_ADJOINT_MINB_NOSRC
-#define ALBM_ADJOINT_MINB_NOSRC 8
+#define ALBM_ADJOINT_MINB_NOSRC 10
 #endif
 // streaming (evict-first) stores for the state and adjoint outputs, which
 // the same kernel never reads back
@@ -89,6 +91,11 @@ template <class S>
 __device__ __forceinline__ float dev_out(const KParams& P, int i, float d) {
   if constexpr (sizeof(S) == 2) return d - P.dev_off[i];
   else return d;
+}
+
+// Element offset of density m at node j + off: m N + j + off.
+__device__ __forceinline__ long long elem(int m, long long N, long long j, long long off = 0) {
+  return (long long)m * N + j + off;
 }
 
 // ---- periodic neighbourhood of one node ----------------------------------
@@ -176,14 +183,13 @@ struct Gather {
                                              const S* __restrict__ B, float* d, float (*g)[QS]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-      d[i] = dev_in<S>(P, i, ld(B + (long long)i * N + geo.idx +
-                                   geo.off(-L::ex(i), -L::ey(i), -L::ez(i))));
+      d[i] = dev_in<S>(P, i, ld(B + elem(i, N, geo.idx, geo.off(-L::ex(i), -L::ey(i), -L::ez(i)))));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int i = 0; i < QS; ++i)
-        g[s][i] = ld(B + (long long)(Q + s * QS + i) * N + geo.idx +
-                     geo.off(-LS::ex(i), -LS::ey(i), -LS::ez(i)));
+        g[s][i] = ld(B + elem(Q + s * QS + i, N, geo.idx,
+                              geo.off(-LS::ex(i), -LS::ey(i), -LS::ez(i))));
   }
 };
 
@@ -209,11 +215,11 @@ __device__ __forceinline__ void primal_body(const KParams& P, const S* __restric
     const float th = theta[idx];
     Ops::template forward<OBJ>(P, type, th, geo.y, d, g, OBJ != 0 && obj != nullptr, o1, o2);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, dev_out<S>(P, i, d[i]));
+    for (int i = 0; i < Q; ++i) st(Bout + elem(i, P.N, idx), dev_out<S>(P, i, d[i]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
-      for (int i = 0; i < QS; ++i) st(Bout + (long long)(Q + s * QS + i) * P.N + idx, g[s][i]);
+      for (int i = 0; i < QS; ++i) st(Bout + elem(Q + s * QS + i, P.N, idx), g[s][i]);
   }
   if (OBJ != 0 && obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
 }
@@ -332,11 +338,11 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
   if (OBJ != 0 && obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
 }
 
-// resident blocks of the paired 16-bit primal (128 threads): 5 keeps it
-// within 96 registers without spills for up to one scalar lattice; two
-// scalars spill at 5 and keep 4
+// resident blocks of the paired 16-bit primal (128 threads): 6 (80
+// registers, a few spilled bytes) measured 1.3 % faster than 5 (96
+// registers) on the exchanger; two scalars keep 4 (they spill at 5)
 #ifndef ALBM_PAIR_MINB
-#define ALBM_PAIR_MINB 5
+#define ALBM_PAIR_MINB 6
 #endif
 template <class L, int NS, bool MRT, class S, int OBJ>
 __global__ void __launch_bounds__(ALBM_PRIMAL_BLOCK, NS >= 2 ? 4 : ALBM_PAIR_MINB) primal_pair_kernel(
@@ -432,14 +438,14 @@ __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __re
 #pragma unroll
       for (int i = 0; i < Q; ++i)
         lam_cp_async4(sl + i * blockDim.x,
-                      lam_in + (long long)i * P.N + idx + geo.off(L::ex(i), L::ey(i), L::ez(i)));
+                      lam_in + elem(i, P.N, idx, geo.off(L::ex(i), L::ey(i), L::ez(i))));
 #pragma unroll
       for (int s = 0; s < NS; ++s)
 #pragma unroll
         for (int i = 0; i < QS; ++i)
           lam_cp_async4(sl + (Q + s * QS + i) * blockDim.x,
-                        lam_in + (long long)(Q + s * QS + i) * P.N + idx +
-                            geo.off(LS::ex(i), LS::ey(i), LS::ez(i)));
+                        lam_in + elem(Q + s * QS + i, P.N, idx,
+                                      geo.off(LS::ex(i), LS::ey(i), LS::ez(i))));
       lam_cp_async_commit();
     }
   }
@@ -461,13 +467,13 @@ __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __re
     } else if (has_next) {
 #pragma unroll
       for (int i = 0; i < Q; ++i)
-        a[i] = __ldg(lam_in + (long long)i * P.N + idx + geo.off(L::ex(i), L::ey(i), L::ez(i)));
+        a[i] = __ldg(lam_in + elem(i, P.N, idx, geo.off(L::ex(i), L::ey(i), L::ez(i))));
 #pragma unroll
       for (int s = 0; s < NS; ++s)
 #pragma unroll
         for (int i = 0; i < QS; ++i)
-          b[s][i] = __ldg(lam_in + (long long)(Q + s * QS + i) * P.N + idx +
-                          geo.off(LS::ex(i), LS::ey(i), LS::ez(i)));
+          b[s][i] = __ldg(lam_in + elem(Q + s * QS + i, P.N, idx,
+                                        geo.off(LS::ex(i), LS::ey(i), LS::ez(i))));
     } else {
 #pragma unroll
       for (int i = 0; i < Q; ++i) a[i] = 0.0f;
@@ -482,11 +488,11 @@ __device__ __forceinline__ void adjoint_body(const KParams& P, const float* __re
   Ops::template reverse<decltype(load), SRC>(P, type, th, geo.y, d, g, load, ws, cbar, lam, lamg,
                                              dth);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) st(lam_out + (long long)i * P.N + idx, lam[i]);
+  for (int i = 0; i < Q; ++i) st(lam_out + elem(i, P.N, idx), lam[i]);
 #pragma unroll
   for (int s = 0; s < NS; ++s)
 #pragma unroll
-    for (int i = 0; i < QS; ++i) st(lam_out + (long long)(Q + s * QS + i) * P.N + idx, lamg[s][i]);
+    for (int i = 0; i < QS; ++i) st(lam_out + elem(Q + s * QS + i, P.N, idx), lamg[s][i]);
   const bool has_theta = type == FLUID || type == INLET || type == OUTLET;
   if (os.theta_out != nullptr || os.overwrite) {
     const float gk = has_theta ? dth : 0.0f;
