@@ -73,7 +73,7 @@ def bytes_per_node(M: int, storage: int, kind: str) -> int:
 # the 256x128x128 lattice (traffic grows with the nodes); valid for the FP32
 # mixer kernels as captured: the forms without objective terms (primal
 # OBJ = 0, adjoint SRC = 0), which run 95 % of the steps.
-TRAFFIC_MIXER_FP32 = {"primal": 1.0298e9, "adjoint": 1.6744e9}
+TRAFFIC_MIXER_FP32 = {"primal": 1.0291e9, "adjoint": 1.6775e9}
 
 
 def workload(args) -> inputs.Problem:
@@ -189,7 +189,26 @@ def oracle_sample(P: inputs.Problem, dims=ORACLE_SAMPLE_DIMS, steps=ORACLE_SAMPL
     return updates / dt / 1e6, dt, torch.get_num_threads(), sample
 
 
-def cpu_baseline_record(P: inputs.Problem) -> dict:
+def cpu_baseline_record(P: inputs.Problem, args) -> dict:
+    """The oracle on the host cores, timed in a fresh process (as the
+    reference arm is: the process that drove the GPU times the host code
+    slower), see cpu_baseline_local."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-only",
+           "--workload", args.workload, "--precision", args.precision]
+    if args.nsteps:
+        cmd += ["--nsteps", str(args.nsteps)]
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT")}
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    for line in out.stdout.splitlines():
+        if line.startswith("{"):
+            rec = json.loads(line)
+            rec["process"] = "fresh host process, no CUDA context"
+            return rec
+    raise RuntimeError(f"cpu baseline process failed: {out.stderr[-2000:]}")
+
+
+def cpu_baseline_local(P: inputs.Problem) -> dict:
     """The oracle on the host cores: all threads torch uses (the reference
     arm's sample and statistic: median of ORACLE_REPEATS runs after one
     warm-up), and one thread on a smaller sample."""
@@ -374,7 +393,7 @@ def run_ours(args):
             line["serving"] = serve_sweep(args)
             line["batch64"] = batch64_record(args)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline_record(P)
+            line["cpu_baseline"] = cpu_baseline_record(P, args)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -834,7 +853,11 @@ def main(argv=None):
                          "exchanger3d, the exchanger) physics on 256x128x64, 6 primal + 6 "
                          "adjoint steps, objective over the last 2 (277 MB per FP32 mixer "
                          "state, > L2)")
+    ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args(argv)
+    if args.cpu_baseline_only:
+        print(json.dumps(cpu_baseline_local(workload(args))), flush=True)
+        return 0
     if args.profile_case:
         return run_profile_case(args)
     if args.workload == "batch64":
