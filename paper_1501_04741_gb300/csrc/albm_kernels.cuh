@@ -173,17 +173,27 @@ __global__ void __launch_bounds__(1024) fold_partials_kernel(const double* __res
                                                             long long nblocks,
                                                             double* __restrict__ out);
 
+// 16-bit primal steps work on the stored values (see ALBM_FOLD_OFFSET)
+template <class S>
+__host__ __device__ constexpr bool fold_offsets() {
+  return ALBM_FOLD_OFFSET && sizeof(S) == 2;
+}
+
 template <class L, int NS, class S>
 struct Gather {
   using LS = typename ScalarOf<L>::type;
   static constexpr int Q = L::Q, QS = LS::Q;
   static constexpr int NSA = NS > 0 ? NS : 1;
   // f^n(x) from B^n: d_j = B_j(x - e_j), g_j = B_{Q+s QS+j}(x - e_j)
+  // RAW: the fluid values as stored (no reference offsets added)
+  template <bool RAW = false>
   __device__ static __forceinline__ void pre(const KParams& P, const Geo& geo, long long N,
                                              const S* __restrict__ B, float* d, float (*g)[QS]) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-      d[i] = dev_in<S>(P, i, ld(B + elem(i, N, geo.idx, geo.off(-L::ex(i), -L::ey(i), -L::ez(i)))));
+    for (int i = 0; i < Q; ++i) {
+      const float raw = ld(B + elem(i, N, geo.idx, geo.off(-L::ex(i), -L::ey(i), -L::ez(i))));
+      d[i] = RAW ? raw : dev_in<S>(P, i, raw);
+    }
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -208,14 +218,15 @@ __device__ __forceinline__ void primal_body(const KParams& P, const S* __restric
   constexpr int Q = Ops::Q, QS = Ops::QS, NSA = Ops::NSA;
   double o1 = 0.0, o2 = 0.0;
   if (idx < P.N) {
+    constexpr bool FOLD = fold_offsets<S>();
     const Geo geo = make_geo(P, idx);
     float d[Q], g[NSA][QS];
-    Gather<L, NS, S>::pre(P, geo, P.N, Bin, d, g);
+    Gather<L, NS, S>::template pre<FOLD>(P, geo, P.N, Bin, d, g);
     const uint8_t type = flags[idx];
     const float th = theta[idx];
-    Ops::template forward<OBJ>(P, type, th, geo.y, d, g, OBJ != 0 && obj != nullptr, o1, o2);
+    Ops::template forward<OBJ, FOLD>(P, type, th, geo.y, d, g, OBJ != 0 && obj != nullptr, o1, o2);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st(Bout + elem(i, P.N, idx), dev_out<S>(P, i, d[i]));
+    for (int i = 0; i < Q; ++i) st(Bout + elem(i, P.N, idx), FOLD ? d[i] : dev_out<S>(P, i, d[i]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -312,8 +323,10 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
     for (int i = 0; i < Q; ++i) {
       gather_pair<S>(Bin + (long long)i * P.N + rowoff(L::ey(i), L::ez(i)), L::ex(i), x, P.nx, da[i],
                      db[i]);
-      da[i] = dev_in<S>(P, i, da[i]);
-      db[i] = dev_in<S>(P, i, db[i]);
+      if constexpr (!fold_offsets<S>()) {
+        da[i] = dev_in<S>(P, i, da[i]);
+        db[i] = dev_in<S>(P, i, db[i]);
+      }
     }
 #pragma unroll
     for (int s = 0; s < NS; ++s)
@@ -324,11 +337,13 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
     const long long idx = row * P.nx + x;
     const float2 th = *reinterpret_cast<const float2*>(theta + idx);
     const uint8_t ta = flags[idx], tb = flags[idx + 1];
-    Ops::template forward<OBJ>(P, ta, th.x, y, da, ga, OBJ != 0 && obj != nullptr, o1, o2);
-    Ops::template forward<OBJ>(P, tb, th.y, y, db, gb, OBJ != 0 && obj != nullptr, o1, o2);
+    constexpr bool FOLD = fold_offsets<S>();
+    Ops::template forward<OBJ, FOLD>(P, ta, th.x, y, da, ga, OBJ != 0 && obj != nullptr, o1, o2);
+    Ops::template forward<OBJ, FOLD>(P, tb, th.y, y, db, gb, OBJ != 0 && obj != nullptr, o1, o2);
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-      Pair<S>::st(Bout + (long long)i * P.N + idx, dev_out<S>(P, i, da[i]), dev_out<S>(P, i, db[i]));
+      Pair<S>::st(Bout + (long long)i * P.N + idx, FOLD ? da[i] : dev_out<S>(P, i, da[i]),
+                  FOLD ? db[i] : dev_out<S>(P, i, db[i]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll

@@ -63,6 +63,20 @@ __host__ __device__ inline int obj_kind(bool active, int objective) {
 #ifndef ALBM_C_LOOP
 #define ALBM_C_LOOP 0
 #endif
+// scalar collision as g + om (geq - g) per population instead of the
+// polynomial form of NodeOps::scalars_forward (same values up to rounding)
+#ifndef ALBM_SCALAR_DIRECT
+#define ALBM_SCALAR_DIRECT 0
+#endif
+// 16-bit storage: the interior-node primal works on the stored values and
+// carries the reference offsets as constants of the moments and of the
+// collision (instead of adding them to every population loaded and
+// subtracting them from every population stored).  Measured slower (the
+// paired kernel spills more with the boundary path beside the folded
+// one: 0.682 -> 0.708 ms on the exchanger), so off by default.
+#ifndef ALBM_FOLD_OFFSET
+#define ALBM_FOLD_OFFSET 0
+#endif
 // fluid collision as two equilibria per population (the direct form of the
 // operator) instead of the polynomial form of NodeOps::collide_fluid
 #ifndef ALBM_COLLIDE_DIRECT
@@ -143,6 +157,9 @@ struct KParams {
   // f_eq,i(1, u_ref) - w_i the equilibrium deviation at the reference
   // velocity (zero for FP32 storage)
   float dev_off[19];
+  // 16-bit storage: sums over the populations of dev_off and of e_i dev_off
+  // (the density and momentum of the reference offsets: 0 and u_ref)
+  float drho_off, j_off[3];
   // n / nx, n / ny and n / (nx / 2) for node, row and pair indices (N < 2^31)
   FastDiv fd_nx, fd_ny, fd_hx;
   // polls a tile-staged kernel waits for a stage's copies (< 0: default)
@@ -169,10 +186,17 @@ template <class L>
 inline void fill_dev_off(const double* u_ref, KParams& k) {
   for (int j = 0; j < 19; ++j) k.dev_off[j] = 0.f;
   const double uu = u_ref[0] * u_ref[0] + u_ref[1] * u_ref[1] + u_ref[2] * u_ref[2];
+  double s0 = 0.0, s1[3] = {0.0, 0.0, 0.0};
   for (int i = 0; i < L::Q; ++i) {
     const double eu = L::ex(i) * u_ref[0] + L::ey(i) * u_ref[1] + L::ez(i) * u_ref[2];
     k.dev_off[i] = (float)(double(L::w(i)) * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+    s0 += k.dev_off[i];
+    s1[0] += L::ex(i) * (double)k.dev_off[i];
+    s1[1] += L::ey(i) * (double)k.dev_off[i];
+    s1[2] += L::ez(i) * (double)k.dev_off[i];
   }
+  k.drho_off = (float)s0;
+  for (int a = 0; a < 3; ++a) k.j_off[a] = (float)s1[a];
 }
 
 // ---------------------------------------------------------------------------
@@ -477,6 +501,11 @@ struct NodeOps {
   // first weighted moments vanish for the stress rows).  Same operator as
   // the direct form (ALBM_COLLIDE_DIRECT), up to rounding.
   // -------------------------------------------------------------------------
+  // With FOLD, d holds the stored values d - dev_off of 16-bit storage on
+  // entry and on exit: the offsets enter the stress moments (their stress
+  // moments are rho = 1, u = u_ref ones) and the output through the
+  // constant (r - 1) dev_off_i.
+  template <bool FOLD = false>
   __device__ static __forceinline__ void collide_fluid(const KParams& P, float* d, float rho,
                                                        float drho, const float* u, const float* v,
                                                        float uu, float vv) {
@@ -500,13 +529,16 @@ struct NodeOps {
 #pragma unroll
         for (int i = 0; i < Q; ++i)
           if (L::U(k, i) != 0) a += float(L::U(k, i)) * d[i];
-        float eq = 0.0f;
+        float eq = 0.0f, eo = 0.0f;
 #pragma unroll
         for (int p_ = 0; p_ < 3; ++p_)
 #pragma unroll
           for (int q_ = 0; q_ < 3; ++q_)
-            if (UW2(k, p_, q_) != 0) eq += (float(UW2(k, p_, q_)) * (4.5f / 36.0f)) * (u[p_] * u[q_]);
-        mk[k] = P.mrt_r[k] * (a - rho * eq);
+            if (UW2(k, p_, q_) != 0) {
+              eq += (float(UW2(k, p_, q_)) * (4.5f / 36.0f)) * (u[p_] * u[q_]);
+              if (FOLD) eo += (float(UW2(k, p_, q_)) * (4.5f / 36.0f)) * (P.j_off[p_] * P.j_off[q_]);
+            }
+        mk[k] = P.mrt_r[k] * (a + eo - rho * eq);
       }
     }
 #pragma unroll
@@ -523,6 +555,7 @@ struct NodeOps {
       for (int a = 0; a < 3; ++a)
         if (e[a] != 0) lin += float(e[a]) * A[a];
       float y = r * d[i] + L::w(i) * (quad + lin);
+      if constexpr (FOLD) y += (r - 1.0f) * P.dev_off[i];
       if constexpr (MRT) {
 #pragma unroll
         for (int k = 0; k < L::NMOM; ++k)
@@ -538,10 +571,48 @@ struct NodeOps {
   // objective form compiled in (see obj_kind): 0 none, 1 outlet/inlet
   // objectives only, 2 all (with the dissipation of every fluid node).
   // -------------------------------------------------------------------------
-  template <int OBJ = 2>
+  template <int OBJ = 2, bool FOLD = false>
   __device__ static __forceinline__ void forward(const KParams& P, uint8_t type, float th, int y,
                                                  float* d, float (*g)[QS], bool want_obj,
                                                  double& obj1, double& obj2) {
+    if constexpr (FOLD) {
+      // d holds the stored values of 16-bit storage (d - dev_off)
+      if (type != FLUID) {
+        // boundary nodes take the deviations themselves
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] += P.dev_off[i];
+        forward<OBJ, false>(P, type, th, y, d, g, want_obj, obj1, obj2);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] -= P.dev_off[i];
+        return;
+      }
+      float sum = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        sum += d[i];
+        if (L::ex(i)) jx += float(L::ex(i)) * d[i];
+        if (L::ey(i)) jy += float(L::ey(i)) * d[i];
+        if (L::ez(i)) jz += float(L::ez(i)) * d[i];
+      }
+      const float drho = sum + P.drho_off;
+      const float rho = 1.0f + drho;
+      const float ir = rcp(rho);
+      float u[3] = {(jx + P.j_off[0]) * ir, (jy + P.j_off[1]) * ir, (jz + P.j_off[2]) * ir};
+      if (OBJ == 2 && want_obj && P.objective == OBJ_DISSIPATION) {
+        float dt[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) dt[i] = d[i] + P.dev_off[i];
+        obj1 += (double)dissipation(P, dt, rho, drho, u);
+      }
+      float G, dG;
+      porosity_G(P, th, G, dG);
+      float v[3] = {G * u[0] + P.gx, G * u[1] + P.gy, G * u[2] + P.gz};
+      const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+      const float vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+      collide_fluid<true>(P, d, rho, drho, u, v, uu, vv);
+      scalars_forward<OBJ>(P, type, th, y, g, u, v, rho, want_obj, obj1, obj2);
+      return;
+    }
     if (type == WALL || type == HOT) {
       float t[Q];
 #pragma unroll
@@ -597,6 +668,17 @@ struct NodeOps {
 #else
     collide_fluid(P, d, rho, drho, u, v, uu, vv);
 #endif
+    scalars_forward<OBJ>(P, type, th, y, g, u, v, rho, want_obj, obj1, obj2);
+  }
+
+  // Scalar lattices of one node after its fluid collision (u: the fluid's
+  // pre-collision or face velocity, v: its post-collision velocity), with
+  // the outlet and inlet objective terms.
+  template <int OBJ>
+  __device__ static __forceinline__ void scalars_forward(const KParams& P, uint8_t type, float th,
+                                                         int y, float (*g)[QS], const float* u,
+                                                         const float* v, float rho, bool want_obj,
+                                                         double& obj1, double& obj2) {
     if (NS == 0) return;
     float om, dom;
     scalar_rate<LS>(P, th, om, dom);
@@ -627,12 +709,29 @@ struct NodeOps {
 #pragma unroll
         for (int i = 0; i < QS; ++i) T += g[s][i];
       }
+#if ALBM_SCALAR_DIRECT
 #pragma unroll
       for (int i = 0; i < QS; ++i) {
         const float ev = float(LS::ex(i)) * v[0] + float(LS::ey(i)) * v[1] + float(LS::ez(i)) * v[2];
         const float geq = LS::w(i) * T * (1.0f + ev * (1.0f / LS::cs2));
         g[s][i] = g[s][i] + om * (geq - g[s][i]);
       }
+#else
+      // (1 - om) g + om geq with om geq_i = w_i (a0 + e_i.a1): node
+      // constants a0 = om T and a1 = om T v / cs2
+      const float a0 = om * T;
+      const float c1 = a0 * (1.0f / LS::cs2);
+      const float a1[3] = {c1 * v[0], c1 * v[1], c1 * v[2]};
+      const float keep = 1.0f - om;
+#pragma unroll
+      for (int i = 0; i < QS; ++i) {
+        float t = a0;
+        if (LS::ex(i)) t += float(LS::ex(i)) * a1[0];
+        if (LS::ey(i)) t += float(LS::ey(i)) * a1[1];
+        if (LS::ez(i)) t += float(LS::ez(i)) * a1[2];
+        g[s][i] = keep * g[s][i] + LS::w(i) * t;
+      }
+#endif
     }
     if (want_obj && type == INLET && P.objective == OBJ_HEATFLUX_DP) {
       obj1 += -0.1 / 3.0 * (double)rho * (double)P.inv_A_in;

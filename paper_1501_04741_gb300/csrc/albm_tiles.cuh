@@ -199,15 +199,20 @@ __global__ void __launch_bounds__(TX) primal_tiles_kernel(KParams P, const S* __
     const S* sb = stage[sg];
     float d[Q], g[NSA][QS];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = dev_in<S>(P, i, to_f(sb[i * W + H + lx - L::ex(i)]));
+    for (int i = 0; i < Q; ++i) {
+      const float raw = to_f(sb[i * W + H + lx - L::ex(i)]);
+      d[i] = fold_offsets<S>() ? raw : dev_in<S>(P, i, raw);
+    }
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int i = 0; i < QS; ++i) g[s][i] = to_f(sb[(Q + s * QS + i) * W + H + lx - LS::ex(i)]);
     double o1 = 0.0, o2 = 0.0;
-    Ops::forward(P, flags[idx], theta[idx], y, d, g, obj != nullptr, o1, o2);
+    Ops::template forward<2, fold_offsets<S>()>(P, flags[idx], theta[idx], y, d, g, obj != nullptr,
+                                                o1, o2);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, dev_out<S>(P, i, d[i]));
+    for (int i = 0; i < Q; ++i)
+      st(Bout + (long long)i * P.N + idx, fold_offsets<S>() ? d[i] : dev_out<S>(P, i, d[i]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -442,15 +447,20 @@ __global__ void __launch_bounds__(TX) primal_async_kernel(KParams P, const S* __
     const S* sb = stage[sg];
     float d[Q], g[NSA][QS];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = dev_in<S>(P, i, to_f(sb[i * W + H + lx - L::ex(i)]));
+    for (int i = 0; i < Q; ++i) {
+      const float raw = to_f(sb[i * W + H + lx - L::ex(i)]);
+      d[i] = fold_offsets<S>() ? raw : dev_in<S>(P, i, raw);
+    }
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int i = 0; i < QS; ++i) g[s][i] = to_f(sb[(Q + s * QS + i) * W + H + lx - LS::ex(i)]);
     double o1 = 0.0, o2 = 0.0;
-    Ops::forward(P, flags[idx], theta[idx], y, d, g, obj != nullptr, o1, o2);
+    Ops::template forward<2, fold_offsets<S>()>(P, flags[idx], theta[idx], y, d, g, obj != nullptr,
+                                                o1, o2);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st(Bout + (long long)i * P.N + idx, dev_out<S>(P, i, d[i]));
+    for (int i = 0; i < Q; ++i)
+      st(Bout + (long long)i * P.N + idx, fold_offsets<S>() ? d[i] : dev_out<S>(P, i, d[i]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
