@@ -452,6 +452,16 @@ def exchanger_precisions(args) -> dict:
             "theta": "Gaussian random field (sigma 4) on the middle 3/7", "rows": rows}
 
 
+def fifo_finish_times(arrivals, service):
+    """Finish times of one server taking requests first come first served:
+    each starts at the later of its arrival and the previous finish."""
+    done, fin = [], 0.0
+    for a, sv in zip(arrivals, service):
+        fin = max(a, fin) + sv
+        done.append(fin)
+    return done
+
+
 def serve_sweep(args) -> dict:
     """Config 5 served with continuous batching at several arrival rates,
     against one-at-a-time plain FP32 FIFO service of the same requests.
@@ -482,10 +492,7 @@ def serve_sweep(args) -> dict:
     rows = []
     for rate in rates:
         arrivals = [t / rate for t, _, _ in spec1]
-        done, fin = [], 0.0
-        for a, sv in zip(arrivals, svc):
-            fin = max(a, fin) + sv
-            done.append(fin)
+        done = fifo_finish_times(arrivals, svc)
         lat_seq = [d - a for d, a in zip(done, arrivals)]
         reqs = [Request(i, a, P, th) for i, (a, (_, P, th)) in enumerate(zip(arrivals, spec1))]
         srv = Server(steps_per_tick=args.tick, keep_gradients=True)

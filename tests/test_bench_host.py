@@ -49,3 +49,13 @@ def test_single_rank_aggregation():
     ms, value = bench.aggregate_ranks(2000.0, 1.0e9, 4, 1, device="cpu")
     assert ms == 2000.0
     assert abs(value - 4.0e9 / 2.0 / 1e6) < 1e-6
+
+
+def test_fifo_finish_times_of_the_one_at_a_time_baseline():
+    from bench import fifo_finish_times
+    # idle server: each request starts on arrival
+    assert fifo_finish_times([0.0, 5.0, 9.0], [1.0, 2.0, 0.5]) == [1.0, 7.0, 9.5]
+    # queueing: a request waits for the previous one to finish
+    assert fifo_finish_times([0.0, 0.1, 0.2], [1.0, 1.0, 1.0]) == [1.0, 2.0, 3.0]
+    # mixed: the third arrives after the queue drained
+    assert fifo_finish_times([0.0, 0.5, 4.0], [2.0, 1.0, 1.0]) == [2.0, 3.0, 5.0]
