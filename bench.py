@@ -73,7 +73,7 @@ def bytes_per_node(M: int, storage: int, kind: str) -> int:
 # the 256x128x128 lattice (traffic grows with the nodes); valid for the FP32
 # mixer kernels as captured: the forms without objective terms (primal
 # OBJ = 0, adjoint SRC = 0), which run 95 % of the steps.
-TRAFFIC_MIXER_FP32 = {"primal": 1.0291e9, "adjoint": 1.6775e9}
+TRAFFIC_MIXER_FP32 = {"primal": 1.0288e9, "adjoint": 1.6775e9}
 
 
 def workload(args) -> inputs.Problem:
