@@ -276,20 +276,23 @@ template <> struct Pair<__half> {
   }
 };
 
+// p points at the word of the pair's own column in the source row; dxm and
+// dxp are the element offsets of the words before and after it (-2 and +2,
+// or across the row's periodic wrap)
 template <class S>
-__device__ __forceinline__ void gather_pair(const S* rowp, int ex, int x, int nx, float& a, float& b) {
+__device__ __forceinline__ void gather_pair(const S* p, int ex, int dxm, int dxp, float& a, float& b) {
   if (ex == 0) {
-    const float2 w = Pair<S>::ld(rowp + x);
+    const float2 w = Pair<S>::ld(p);
     a = w.x;
     b = w.y;
   } else if (ex > 0) {  // sources x - 1, x
-    const float2 w0 = Pair<S>::ld(rowp + (x == 0 ? nx - 2 : x - 2));
-    const float2 w1 = Pair<S>::ld(rowp + x);
+    const float2 w0 = Pair<S>::ld(p + dxm);
+    const float2 w1 = Pair<S>::ld(p);
     a = w0.y;
     b = w1.x;
   } else {              // sources x + 1, x + 2
-    const float2 w1 = Pair<S>::ld(rowp + x);
-    const float2 w2 = Pair<S>::ld(rowp + (x + 2 == nx ? 0 : x + 2));
+    const float2 w1 = Pair<S>::ld(p);
+    const float2 w2 = Pair<S>::ld(p + dxp);
     a = w1.y;
     b = w2.x;
   }
@@ -313,16 +316,24 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
     const int y = (int)(rw - (unsigned)z * (unsigned)P.ny);
     const int ym = y == 0 ? P.ny - 1 : y - 1, yp = y == P.ny - 1 ? 0 : y + 1;
     const int zm = z == 0 ? P.nz - 1 : z - 1, zp = z == P.nz - 1 ? 0 : z + 1;
-    auto rowoff = [&](int ey, int ez) -> long long {  // source row of shift (ey, ez)
+    // One 64-bit base pointer at the pair's first node; every gather and
+    // store is a 32-bit element offset from it (the state has fewer than
+    // 2^31 elements: checked by the launcher), density m at m N plus the
+    // source row's shift.
+    const long long idx = row * P.nx + x;
+    const int N32 = (int)P.N;
+    auto rowrel = [&](int ey, int ez) -> int {  // source row of shift (ey, ez), relative
       const int ys = ey > 0 ? ym : (ey < 0 ? yp : y);
       const int zs = ez > 0 ? zm : (ez < 0 ? zp : z);
-      return ((long long)zs * P.ny + ys) * P.nx;
+      return ((zs - z) * P.ny + (ys - y)) * P.nx;
     };
+    const int dxm = (x == 0 ? P.nx - 2 : x - 2) - x;
+    const int dxp = (x + 2 == P.nx ? 0 : x + 2) - x;
+    const S* bin = Bin + idx;
     float da[Q], db[Q], ga[NSA][QS], gb[NSA][QS];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      gather_pair<S>(Bin + (long long)i * P.N + rowoff(L::ey(i), L::ez(i)), L::ex(i), x, P.nx, da[i],
-                     db[i]);
+      gather_pair<S>(bin + (i * N32 + rowrel(L::ey(i), L::ez(i))), L::ex(i), dxm, dxp, da[i], db[i]);
       if constexpr (!fold_offsets<S>()) {
         da[i] = dev_in<S>(P, i, da[i]);
         db[i] = dev_in<S>(P, i, db[i]);
@@ -332,23 +343,22 @@ __device__ __forceinline__ void primal_pair_body(const KParams& P, const S* __re
     for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int i = 0; i < QS; ++i)
-        gather_pair<S>(Bin + (long long)(Q + s * QS + i) * P.N + rowoff(LS::ey(i), LS::ez(i)),
-                       LS::ex(i), x, P.nx, ga[s][i], gb[s][i]);
-    const long long idx = row * P.nx + x;
+        gather_pair<S>(bin + ((Q + s * QS + i) * N32 + rowrel(LS::ey(i), LS::ez(i))), LS::ex(i), dxm,
+                       dxp, ga[s][i], gb[s][i]);
     const float2 th = *reinterpret_cast<const float2*>(theta + idx);
     const uint8_t ta = flags[idx], tb = flags[idx + 1];
     constexpr bool FOLD = fold_offsets<S>();
     Ops::template forward<OBJ, FOLD>(P, ta, th.x, y, da, ga, OBJ != 0 && obj != nullptr, o1, o2);
     Ops::template forward<OBJ, FOLD>(P, tb, th.y, y, db, gb, OBJ != 0 && obj != nullptr, o1, o2);
+    S* bout = Bout + idx;
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-      Pair<S>::st(Bout + (long long)i * P.N + idx, FOLD ? da[i] : dev_out<S>(P, i, da[i]),
+      Pair<S>::st(bout + i * N32, FOLD ? da[i] : dev_out<S>(P, i, da[i]),
                   FOLD ? db[i] : dev_out<S>(P, i, db[i]));
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
-      for (int i = 0; i < QS; ++i)
-        Pair<S>::st(Bout + (long long)(Q + s * QS + i) * P.N + idx, ga[s][i], gb[s][i]);
+      for (int i = 0; i < QS; ++i) Pair<S>::st(bout + (Q + s * QS + i) * N32, ga[s][i], gb[s][i]);
   }
   if (OBJ != 0 && obj != nullptr) block_partial2(o1, o2, obj + 2 * (long long)block);
 }
@@ -768,8 +778,12 @@ constexpr int kBlock = 256;
 template <class L, int NS, bool MRT, class S>
 struct Launch {
   static unsigned blocks(const KParams& P) { return (unsigned)((P.N + kBlock - 1) / kBlock); }
-  // 16-bit storage with an even nx runs two nodes per thread
-  static bool paired(const KParams& P) { return sizeof(S) == 2 && (P.nx % 2) == 0; }
+  // 16-bit storage with an even nx runs two nodes per thread (element
+  // offsets within one state in 32 bits: fewer than 2^31 elements)
+  static bool paired(const KParams& P) {
+    return sizeof(S) == 2 && (P.nx % 2) == 0 &&
+           (long long)(L::Q + NS * ScalarOf<L>::type::Q) * P.N < (1LL << 31);
+  }
   static cudaError_t primal(const KParams& P, const StepArgs& a, cudaStream_t st) {
     if constexpr (sizeof(S) == 2) {
       if (paired(P)) {
